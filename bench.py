@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable ERP Gaussian rasterizer on one GB300 (and N replicas).
+
+One step = one forward + backward iteration of the whole hot path on the headline workload:
+1M Gaussians (SH degree 3, 20% near the poles, 20% on the longitude seam), one 2048x1024 ERP
+view: preprocess -> depth sort + tile binning + tile sort -> forward blend -> L1 loss against a
+noise target (torch) -> backward blend -> chain rule to all parameter gradients.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on bounded pixel
+samples of the same workload instead (the CPU baseline; it never touches the GPU).
+Under torchrun (N > 1) every rank runs an independent replica of the workload (weak scaling; the
+path has no data exchange between frames) and rank 0 reports the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ERP fwd+bwd iter/s at 1M Gaussians 2048×1024 (1 GB300); batched views/s vs single"
+UNIT = "iter/s"
+WORKLOAD = "config2: 1,000,000 Gaussians (SH3; 20% within 10 deg of the poles, 20% within 5 deg of the seam), " \
+           "one 2048x1024 ERP view, fwd+bwd with L1 loss"
+CPU_SAMPLE_PIXELS = 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=1_000_000, help="Gaussians (headline: 1M)")
+    ap.add_argument("--width", type=int, default=2048)
+    ap.add_argument("--tile", type=str, default="16x16")
+    ap.add_argument("--batch", type=int, default=64)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def _gpu_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ algorithmic work
+
+# FP32 flops (FMA = 2) per (pixel, list entry) of the blend, as the method needs them:
+#   every tested entry: pixel offset (2), quadratic form of Eq. 2 with log-opacity (8), test (1)
+#   every blended entry, forward: exp (1), clamp (1), 1 - alpha (1), T' (1), test (1), alpha T (1),
+#                                 colour accumulation (6)
+#   every blended entry, backward: exp, clamp, 1 - alpha, T recovery, weight (5), rgb.g (5),
+#                                 dL/dalpha (3), B update (2), dL/drgb (3), dL/dpower (1),
+#                                 dL/do (1), dL/dconic (6), dL/d(u, v) (8)
+FLOP_TESTED = 11
+FLOP_BLEND_FWD = 12
+FLOP_BLEND_BWD = 34
+
+
+def fp32_peak_tflops(torch, dev, peaks):
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(scene, n_pix, seed=0):
+    """Oracle forward + adjoint on n_pix seeded pixels; returns timings and the extrapolated
+    full-frame iteration time."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2410_20686_gb300 import scenes as S
+    v = scene.views[0]
+    p = O.Params.of(scene)
+    st = O.Settings(sh_degree=scene.sh_degree, dilation=float(np.float32(0.3)), r_near=float(np.float32(0.2)),
+                    r_far=float(np.float32(1e4)))
+    pix = S.sample_pixels(v.width, v.height, n_pix, [], seed=seed)
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=(len(pix), 3))
+    t0 = time.perf_counter()
+    O.render(p, v, st, pix=pix[:1])
+    t1 = time.perf_counter()
+    O.render(p, v, st, pix=pix)
+    t2 = time.perf_counter()
+    O.backward(p, v, st, g[:1], pix=pix[:1])
+    t3 = time.perf_counter()
+    O.backward(p, v, st, g, pix=pix)
+    t4 = time.perf_counter()
+    fixed = (t1 - t0) + (t3 - t2)              # per-Gaussian projection, sort, adjoint chain
+    per_pix = ((t2 - t1) + (t4 - t3)) / max(len(pix) - 1, 1)
+    full = fixed + per_pix * v.width * v.height
+    return {"sample_s": t4 - t0, "full_iter_s": full, "pixels": len(pix), "threads": O.num_threads()}
+
+
+def cpu_baseline(scene):
+    r = oracle_sample(scene, CPU_SAMPLE_PIXELS)
+    return {"value": 1.0 / r["full_iter_s"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+            "sample": f"{r['pixels']} seeded pixels of the 2048x1024 view, forward + adjoint, per-pixel time "
+                      f"extrapolated to all pixels plus the full per-Gaussian projection / adjoint "
+                      f"({r['sample_s']:.1f} s of CPU work)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2410_20686_gb300 import scenes as S
+    from oracle import oracle as O
+    O.build()
+    scene = S.config2(n=args.n, width=args.width)
+    for w in range(args.warmup):
+        oracle_sample(scene, 64, seed=100 + w)
+    times = []
+    res = None
+    for k in range(args.steps):
+        res = oracle_sample(scene, 256, seed=k)
+        times.append(res["full_iter_s"])
+    import statistics
+    full = statistics.median(times)
+    value = 1.0 / full
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+                            "sample": "each step: 256 seeded pixels, forward + adjoint, extrapolated to the full frame"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_20686_gb300 import build as B
+    from paper_2410_20686_gb300 import scenes as S
+    from paper_2410_20686_gb300.rasterizer import Rasterizer, RenderSettings
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    tw, th = (int(x) for x in args.tile.split("x"))
+    rs = RenderSettings(sh_degree=3, tile_w=tw, tile_h=th, batch=args.batch)
+    scene = S.config2(n=args.n, width=args.width)
+    target_np = S.target_images(scene, 2)[0]
+    view = scene.views[0]
+    params = [torch.tensor(a, device=dev) for a in (scene.means, scene.scales, scene.quats, scene.opacity, scene.sh)]
+    target = torch.tensor(target_np, device=dev)
+    grads = {k: torch.empty_like(t) for k, t in zip(("means", "scales", "quats", "opacity", "sh"), params)}
+    rast = Rasterizer(dev, capacity_mode="query", headroom=1.1)
+
+    evs = None
+
+    def step(record=None):
+        if record is not None:
+            record[0].record()
+        rast.preprocess(*params, [view], rs)
+        if record is not None:
+            record[1].record()
+        rast.bin_sort()
+        if record is not None:
+            record[2].record()
+        imgs, _ = rast.render_fwd(want_T=False)
+        if record is not None:
+            record[3].record()
+        diff = imgs[0] - target
+        loss = diff.abs().mean()
+        g = torch.sign(diff) * (1.0 / diff.numel())  # dL/dC of the mean absolute error
+        if record is not None:
+            record[4].record()
+        rast.render_bwd([g])
+        if record is not None:
+            record[5].record()
+        rast.preprocess_bwd(grads)
+        if record is not None:
+            record[6].record()
+        return loss
+
+    # size the pair buffer once, then run without host synchronisation
+    step()
+    torch.cuda.synchronize()
+    rast.capacity_mode = "fixed"
+    stats = rast.stats()
+    assert stats["status"] == 0, stats
+    launches_per_step = rast.launch_count()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(_gpu_id(torch, local))
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    start.record()
+    for i in range(K):
+        step(evs[i])
+    stop.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed = start.elapsed_time(stop) / 1e3
+    t = torch.tensor([elapsed], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    stats = rast.stats()
+    assert stats["status"] == 0, stats
+
+    names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
+    kern = {nm: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)])) for j, nm in enumerate(names)}
+
+    # end-to-end through host buffers: parameters and target copied in from pinned memory each
+    # step, the loss read back
+    e2e = None
+    if not args.no_e2e:
+        host = [t_.cpu().pin_memory() for t_ in params] + [target.cpu().pin_memory()]
+        dev_bufs = params + [target]
+        h2d = sum(h.numel() * h.element_size() for h in host)
+
+        def e2e_step():
+            for h, d in zip(host, dev_bufs):
+                d.copy_(h, non_blocking=True)
+            loss = step()
+            return loss.item()
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * K / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = _peaks()
+    peak_tf, sms, mhz = fp32_peak_tflops(torch, dev, peaks)
+    fwd_flops = FLOP_TESTED * stats["evals_fwd"] + FLOP_BLEND_FWD * stats["blended"]
+    bwd_flops = FLOP_TESTED * stats["evals_bwd"] + FLOP_BLEND_BWD * stats["blended"]
+    dom = max(("render_fwd", "render_bwd"), key=lambda k: kern[k])
+    dom_flops = fwd_flops if dom == "render_fwd" else bwd_flops
+    achieved = dom_flops / (kern[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_render_fwd" if dom == "render_fwd" else "k_render_bwd",
+                "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                "traffic": None,
+                "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (max SM clock, "
+                             f"{peak_src} peaks file)",
+                "units": {"evals_fwd": stats["evals_fwd"], "evals_bwd": stats["evals_bwd"],
+                          "blended": stats["blended"], "pairs": stats["pairs"]}}
+
+    out = {"metric": METRIC, "value": world * K / elapsed, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2,
+                      "sh_degree": 3, "tile": args.tile, "batch": args.batch,
+                      "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "kernels_ms": kern, "gpu_launches": launches_per_step * K, "clocks": clocks}
+    if e2e:
+        out["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * odgs.h -- C ABI of the GB300 (sm_103a) differentiable omnidirectional Gaussian rasterizer.
+ *
+ * The library renders 3D Gaussians into equirectangular (ERP) images and back-propagates
+ * image gradients to the Gaussian parameters, as described by ODGS (arXiv 2410.20686):
+ *   - projection of each Gaussian onto the tangent plane of the unit sphere at its centre and
+ *     the ERP Jacobian J_omni (Sec. 3.2, Eq. 4-8), Sigma_2D = J_omni W Sigma W^T J_omni^T;
+ *   - spherical-shell culling (Sec. 3.2), view-dependent colour from spherical harmonics;
+ *   - depth-ordered front-to-back alpha blending of the 2D Gaussians (Sec. 3.1, Eq. 2-3);
+ *   - the backward pass of App. A.3 (Eq. 11 and the Jacobian's dependence on the mean).
+ *
+ * Call sequence for one frame (one or many views of the same Gaussians):
+ *   odgs_preprocess -> [odgs_query_pairs] -> odgs_bin_sort -> odgs_render_fwd
+ *   -> odgs_render_bwd -> odgs_preprocess_bwd
+ * All compute calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*;
+ * NULL = legacy default stream). Only odgs_query_pairs, odgs_get_status and odgs_frame_stats
+ * synchronize.
+ *
+ * Memory: the caller owns every buffer. Device pointers below point to device memory; the
+ * structs themselves and the pointer arrays (images, final_T, dL_dimages) live in host memory
+ * and are read during the call. The library allocates no device memory: its scratch is the
+ * caller's "workspace" (sized by odgs_workspace_size) and "pair buffer" (sized by
+ * odgs_pair_buffer_size). Both must stay allocated, and the Gaussian arrays unchanged, from
+ * odgs_preprocess until the last call of the frame (dL_dimages until odgs_render_bwd has
+ * been followed by odgs_preprocess_bwd). Host state lives in an odgs_ctx.
+ *
+ * Errors: argument errors are returned synchronously (nothing is launched). CUDA launch errors
+ * return ODGS_ERR_CUDA. Errors found on the device (pair capacity exceeded, a bounded wait
+ * that gave up) set bits in a device status word: the kernels skip the work they cannot do
+ * without writing out of bounds, and odgs_query_pairs / odgs_get_status report the bits.
+ */
+#ifndef ODGS_H
+#define ODGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ODGS_OK = 0,
+    ODGS_ERR_INVALID_ARG = -1, /* bad pointer, size, layout or setting; nothing launched      */
+    ODGS_ERR_CAPACITY = -2,    /* more tile/Gaussian pairs than the pair buffer holds          */
+    ODGS_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed                  */
+    ODGS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up (results are invalid)     */
+    ODGS_ERR_STATE = -6,       /* calls made out of order (e.g. render before bin_sort)        */
+    ODGS_ERR_WORKSPACE = -7    /* workspace or pair buffer smaller than required               */
+} odgs_status;
+
+/* Device status word bits, reported by odgs_get_status. */
+#define ODGS_DEV_CAPACITY 1u
+#define ODGS_DEV_TIMEOUT 2u
+
+#define ODGS_MAX_VIEWS 64
+
+/* One ERP camera. World point mu maps to camera space as t = R_wc mu + t_wc, with OpenCV
+ * axes (x right, y down, z forward; Sec. 3.2). Pixel (i, j) is sampled at (i + 0.5, j + 0.5)
+ * of the ERP plane of Eq. 4: u = W/(2 pi) phi + W/2, v = -H/pi theta + H/2. */
+typedef struct {
+    int width, height; /* W must be a multiple of the tile width; any H >= 1   */
+    float R_wc[9];     /* row-major world -> camera rotation                    */
+    float t_wc[3];
+} odgs_view;
+
+typedef struct {
+    int sh_degree;      /* 0..3; colour = max(0, sum_k sh_k Y_k(d) + 0.5)               */
+    int sh_coeffs;      /* coefficients stored per Gaussian in sh (>= (deg+1)^2)        */
+    int tile_w, tile_h; /* pixel tile; 0 -> 16 x 16. tile_w * tile_h in [32, 1024],
+                           tile_w in {8, 16, 32}                                       */
+    int batch;          /* Gaussians staged per shared-memory batch; 0 -> 64 (<= 256)   */
+    float cov_dilation; /* added to both diagonals of Sigma_2D (px^2); e.g. 0.3          */
+    float r_near, r_far;/* spherical-shell culling radii (Sec. 3.2); e.g. 0.2, 1e4       */
+    float bg[3];        /* background colour blended with the final transmittance        */
+    int recompute_lists;/* 1: odgs_render_bwd re-runs preprocess + bin_sort itself        */
+    int grad_accumulate;/* 1: gradients are added (+=) to the output arrays; 0: written  */
+} odgs_settings;
+
+/* Gaussian parameters, device pointers, float32, contiguous:
+ *   means [n][3], scales [n][3] (activated, > 0), quats [n][4] (w, x, y, z; normalized by the
+ *   library), opacity [n] (activated, in (0, 1)), sh [n][sh_coeffs][3] (16-byte aligned when
+ *   3*sh_coeffs is a multiple of 4). n >= 0. */
+typedef struct {
+    const float *means, *scales, *quats, *opacity, *sh;
+    int n;
+} odgs_gaussians;
+
+/* Parameter gradients, device pointers with the layouts of odgs_gaussians. */
+typedef struct {
+    float *means, *scales, *quats, *opacity, *sh;
+} odgs_grads;
+
+typedef struct odgs_ctx odgs_ctx;
+
+/* Create / destroy host-side state for the current CUDA device. Creating queries the device
+ * (SM count, occupancy); it allocates host memory only. */
+odgs_status odgs_create(odgs_ctx **out);
+void odgs_destroy(odgs_ctx *ctx);
+
+/* Bytes of device workspace needed for n Gaussians and these views (host-only, pure). */
+odgs_status odgs_workspace_size(int n, const odgs_view *views, int n_views, const odgs_settings *s,
+                                size_t *bytes);
+
+/* Bytes of pair buffer for up to pair_capacity (tile, Gaussian) pairs (< 2^30). */
+odgs_status odgs_pair_buffer_size(size_t pair_capacity, size_t *bytes);
+
+/* Per Gaussian and view (Sec. 3.1-3.2, Eq. 4-8): covariance, camera transform, shell culling,
+ * ERP mean and covariance, SH colour, conservative tile rectangle with longitude-seam wrap and
+ * pole stretch, depth key. Also counts the (tile, Gaussian) pairs of the frame. */
+odgs_status odgs_preprocess(odgs_ctx *ctx, const odgs_gaussians *g, const odgs_view *views,
+                            int n_views, const odgs_settings *s, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
+/* Synchronizes the stream; returns the number of pairs the last odgs_preprocess produced
+ * and, as the return value, the first error recorded on the device (or ODGS_OK). */
+odgs_status odgs_query_pairs(odgs_ctx *ctx, size_t *pairs, void *stream);
+
+/* Depth sort, per-tile pair emission and stable tile sort (the "sorting by depth" of Sec.
+ * 3.1, binned into ERP tiles), then per-tile list ranges. Pairs beyond pair_capacity are
+ * dropped and set ODGS_DEV_CAPACITY. */
+odgs_status odgs_bin_sort(odgs_ctx *ctx, void *pair_buffer, size_t pair_capacity, void *stream);
+
+/* Front-to-back alpha blending of Eq. 3 for every view in one persistent launch.
+ * images[v]: device [3][H][W] float32 (channel-major); final_T[v]: device [H][W] or NULL
+ * (the array final_T itself may be NULL). */
+odgs_status odgs_render_fwd(odgs_ctx *ctx, float *const *images, float *const *final_T, void *stream);
+
+/* Backward pass, part 1: reverse of the blend of Eq. 3 per pixel (back to front from each
+ * pixel's last blended Gaussian), accumulating per (view, Gaussian) the gradients w.r.t. its ERP
+ * mean, conic, opacity and colour in the workspace. dL_dimages[v]: device [3][H][W] float32.
+ * With recompute_lists = 1 it first re-runs odgs_preprocess and odgs_bin_sort (identical lists). */
+odgs_status odgs_render_bwd(odgs_ctx *ctx, const float *const *dL_dimages, void *stream);
+
+/* Backward pass, part 2: chain rule from the accumulated screen-space gradients to the Gaussian
+ * parameters (App. A.3: Eq. 11, dL/dJ = dL/dT W^T, the dependence of J_omni on the mean, the
+ * mean path of Eq. 10, SH colour, quaternion and scale), summed over all views. Writes (or
+ * adds, per grad_accumulate) all five gradient arrays. */
+odgs_status odgs_preprocess_bwd(odgs_ctx *ctx, const odgs_grads *grads, void *stream);
+
+/* Work counters of the current frame, read back after a stream synchronization. */
+typedef struct {
+    uint64_t pairs;         /* (tile, Gaussian) pairs counted by odgs_preprocess              */
+    uint64_t pairs_sorted;  /* pairs emitted and sorted (min(pairs, capacity))                */
+    uint64_t evals_fwd;     /* (pixel, list entry) evaluations of the last odgs_render_fwd    */
+    uint64_t evals_bwd;     /* (pixel, list entry) evaluations of the last odgs_render_bwd    */
+    uint64_t blended;       /* (pixel, Gaussian) pairs blended by the last odgs_render_fwd    */
+    uint32_t status;        /* device status bits (ODGS_DEV_*)                                */
+} odgs_stats;
+
+odgs_status odgs_frame_stats(odgs_ctx *ctx, odgs_stats *out, void *stream);
+
+/* Synchronizes the stream and returns the device status bits (ODGS_DEV_*) in *bits. */
+odgs_status odgs_get_status(odgs_ctx *ctx, uint32_t *bits, void *stream);
+
+/* Kernel launches the last frame issued (for accounting). */
+int odgs_last_launch_count(const odgs_ctx *ctx);
+
+const char *odgs_status_string(odgs_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ODGS_H */

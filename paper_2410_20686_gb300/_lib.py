@@ -1,0 +1,122 @@
+"""ctypes mirror of ``include/odgs.h`` (argument marshalling only).
+
+Loading fails loudly if ``libodgs.so`` has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libodgs.so")
+
+ODGS_OK = 0
+STATUS_NAMES = {0: "ODGS_OK", -1: "ODGS_ERR_INVALID_ARG", -2: "ODGS_ERR_CAPACITY", -3: "ODGS_ERR_CUDA",
+                -4: "ODGS_ERR_TIMEOUT", -6: "ODGS_ERR_STATE", -7: "ODGS_ERR_WORKSPACE"}
+DEV_CAPACITY = 1
+DEV_TIMEOUT = 2
+MAX_VIEWS = 64
+
+# every symbol include/odgs.h declares
+EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buffer_size",
+            "odgs_preprocess", "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd",
+            "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
+            "odgs_last_launch_count", "odgs_status_string")
+
+
+class OdgsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({status_string(status)})")
+
+
+class View(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("R_wc", C.c_float * 9), ("t_wc", C.c_float * 3)]
+
+
+class Settings(C.Structure):
+    _fields_ = [("sh_degree", C.c_int), ("sh_coeffs", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int),
+                ("batch", C.c_int), ("cov_dilation", C.c_float), ("r_near", C.c_float), ("r_far", C.c_float),
+                ("bg", C.c_float * 3), ("recompute_lists", C.c_int), ("grad_accumulate", C.c_int)]
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("pairs", C.c_uint64), ("pairs_sorted", C.c_uint64), ("evals_fwd", C.c_uint64),
+                ("evals_bwd", C.c_uint64), ("blended", C.c_uint64), ("status", C.c_uint32)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"ODGS CUDA library not built: {path} is missing (run "
+                          f"paper_2410_20686_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, sz = C.c_void_p, C.c_size_t
+    L.odgs_create.argtypes = [C.POINTER(C.c_void_p)]
+    L.odgs_destroy.argtypes = [vp]
+    L.odgs_destroy.restype = None
+    L.odgs_workspace_size.argtypes = [C.c_int, C.POINTER(View), C.c_int, C.POINTER(Settings), C.POINTER(sz)]
+    L.odgs_pair_buffer_size.argtypes = [sz, C.POINTER(sz)]
+    L.odgs_preprocess.argtypes = [vp, C.POINTER(Gaussians), C.POINTER(View), C.c_int, C.POINTER(Settings),
+                                  vp, sz, vp]
+    L.odgs_query_pairs.argtypes = [vp, C.POINTER(sz), vp]
+    L.odgs_bin_sort.argtypes = [vp, vp, sz, vp]
+    L.odgs_render_fwd.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), vp]
+    L.odgs_render_bwd.argtypes = [vp, C.POINTER(vp), vp]
+    L.odgs_preprocess_bwd.argtypes = [vp, C.POINTER(Grads), vp]
+    L.odgs_frame_stats.argtypes = [vp, C.POINTER(Stats), vp]
+    L.odgs_get_status.argtypes = [vp, C.POINTER(C.c_uint32), vp]
+    L.odgs_last_launch_count.argtypes = [vp]
+    L.odgs_last_launch_count.restype = C.c_int
+    L.odgs_status_string.argtypes = [C.c_int]
+    L.odgs_status_string.restype = C.c_char_p
+    for name in ("odgs_create", "odgs_workspace_size", "odgs_pair_buffer_size", "odgs_preprocess",
+                 "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
+                 "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def status_string(st: int) -> str:
+    try:
+        return load().odgs_status_string(int(st)).decode()
+    except ImportError:
+        return STATUS_NAMES.get(st, str(st))
+
+
+def check(st: int, where: str):
+    if st != ODGS_OK:
+        raise OdgsError(st, where)
+
+
+def make_view(width, height, R_wc, t_wc) -> View:
+    v = View()
+    v.width, v.height = int(width), int(height)
+    v.R_wc[:] = [float(x) for x in list(_flat(R_wc))]
+    v.t_wc[:] = [float(x) for x in list(_flat(t_wc))]
+    return v
+
+
+def _flat(a):
+    try:
+        import numpy as np
+        return np.asarray(a, dtype=np.float32).ravel().tolist()
+    except Exception:  # pragma: no cover
+        return list(a)

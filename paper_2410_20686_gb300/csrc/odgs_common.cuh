@@ -1,0 +1,191 @@
+// Device-side definitions shared by the ODGS kernels (sm_103a).
+//
+// Record layout per (view, Gaussian) item, written by the preprocess kernel and gathered by the
+// blend kernels (16-byte vector loads):
+//   rec_a = { du, dv, bits(c0 | r0 << 16), opacity }   ERP mean = (c0 + 0.5 + du, r0 + 0.5 + dv)
+//   rec_b = { conic_a, conic_b, conic_c, 0 }            inverse of Sigma_2D (Eq. 8, dilated)
+//   rec_c = { r, g, b, 0 }                              SH colour
+// The mean is stored as an integer pixel anchor plus a small float offset so that the offset
+// from any pixel centre, (i - c0) - du, is formed without the rounding error of a float
+// coordinate near W (about 1e-4 px at W = 2048).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace odgs {
+
+constexpr int kMaxViews = 64;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+// alpha >= 1/255 is decided on the base-2 exponent p of alpha = 2^p: p >= log2(1/255).
+constexpr float kLog2AlphaMin = -7.99435343685886f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kPi = 3.14159265358979323846f;
+
+// device status bits (mirrors ODGS_DEV_* in odgs.h)
+constexpr uint32_t kStCapacity = 1u;
+constexpr uint32_t kStTimeout = 2u;
+
+// Per-view constants, uploaded once per frame into the workspace.
+struct ViewDev {
+    int W, H, tiles_x, tiles_y;
+    int tile_base;  // first global tile id of this view
+    int pix_base;   // first global pixel index of this view
+    int trig_u;     // float4 offset of the per-column (cos, sin) table
+    int trig_v;     // float4 offset of the per-row (cos, sin) table
+    float R[9];
+    float t[3];
+    float cam[3];   // camera centre in world space, -R^T t
+    float fx, fy;   // W / (2 pi), H / pi
+    float pad[3];
+};
+
+// Device header at the start of the workspace.
+struct Header {
+    unsigned long long pairs;         // total (tile, Gaussian) pairs counted by the preprocess
+    unsigned long long pairs_emitted; // min(pairs, capacity) used by the tile sort
+    unsigned long long evals_fwd;     // (pixel, entry) evaluations of the last forward blend
+    unsigned long long evals_bwd;     // (pixel, entry) evaluations of the last backward blend
+    unsigned long long blended;       // (pixel, entry) pairs blended by the last forward pass
+    uint32_t status;
+    uint32_t n_items;                 // views * n
+    uint32_t n_pairs_sort;            // 32-bit copy of pairs_emitted for the sort kernels
+    uint32_t work_fwd;
+    uint32_t work_bwd;
+    uint32_t pad[1];
+};
+
+struct Settings {
+    int sh_degree, sh_coeffs;
+    int tile_w, tile_h;
+    float dilation, r_near, r_far;
+    float bg[3];
+};
+
+// ------------------------------------------------------------------ float-float arithmetic
+// Unevaluated sums hi + lo (Dekker 1971; Knuth's TwoSum), used only to place the ERP mean
+// precisely. Every operation is written with round-to-nearest intrinsics so the compiler can
+// neither contract nor reorder it.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float v = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+    return {s, e};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    ff p = two_prod(a.hi, b.hi);
+    float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    return quick_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+    ff p = two_prod(a.hi, b);
+    return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+    float s = __fsqrt_rn(a.hi);
+    if (!(s > 0.f)) return {s, 0.f};
+    float r = __fmaf_rn(-s, s, a.hi);  // exact residual a.hi - s^2
+    float e = __fdiv_rn(__fadd_rn(r, a.lo), __fmul_rn(2.f, s));
+    return quick_two_sum(s, e);
+}
+
+// ------------------------------------------------------------------ blend evaluation
+// Staged form of one list entry for a given tile (identical in the forward and backward
+// kernels, so both take the same skip / clamp / termination decisions bit for bit).
+struct Staged {
+    float4 pos;  // fc (column anchor, incl. seam shift), fr (row anchor), du, dv
+    float4 con;  // A, B, C, log2(o): p = log2(o) + dx (A dx + B dy) + C dy^2
+    float4 col;  // r, g, b, fsplit (first column using fc2; +inf if none)
+    float fc2;   // column anchor right of the seam split
+};
+
+// Seam shift for pixel column i: the image of the Gaussian nearest to the pixel, so that the
+// horizontal offset lies in [-W/2, W/2).
+__device__ __forceinline__ int seam_shift(int i, int c0, float du, int W) {
+    float dx0 = __fsub_rn((float)(i - c0), du);
+    float half = 0.5f * (float)W;
+    if (dx0 >= half) return W;
+    if (dx0 < -half) return -W;
+    return 0;
+}
+
+__device__ __forceinline__ Staged stage_entry(float4 ra, float4 rb, float4 rc, int x0, int tw, int W) {
+    Staged s;
+    uint32_t packed = __float_as_uint(ra.z);
+    int c0 = (int)(packed & 0xFFFFu);
+    int r0 = (int)(packed >> 16);
+    int s0 = seam_shift(x0, c0, ra.x, W);
+    int s1 = seam_shift(x0 + tw - 1, c0, ra.x, W);
+    float fsplit = __int_as_float(0x7f800000);  // +inf
+    float fc2 = (float)(c0 + s1);
+    if (s0 != s1) {
+        int xs = x0 + 1;
+        while (xs < x0 + tw - 1 && seam_shift(xs, c0, ra.x, W) == s0) ++xs;
+        fsplit = (float)xs;
+    }
+    s.pos = make_float4((float)(c0 + s0), (float)r0, ra.x, ra.y);
+    const float k = -0.5f * kLog2e;
+    s.con = make_float4(__fmul_rn(rb.x, k), __fmul_rn(rb.y, -kLog2e), __fmul_rn(rb.z, k), log2f(ra.w));
+    s.col = make_float4(rc.x, rc.y, rc.z, fsplit);
+    s.fc2 = fc2;
+    return s;
+}
+
+// Gathers an item's three records; an index past the end (possible only after a sort that gave
+// up, with the status already set) yields an entry that never passes the alpha test.
+__device__ __forceinline__ void gather_records(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                               const float4* __restrict__ rc, uint32_t idx, uint32_t n_items,
+                                               float4& a, float4& b, float4& c) {
+    if (idx < n_items) {
+        a = ra[idx]; b = rb[idx]; c = rc[idx];
+    } else {
+        a = make_float4(0.f, 0.f, 0.f, 0.f);  // opacity 0 -> log2(o) = -inf
+        b = make_float4(1.f, 0.f, 1.f, 0.f);
+        c = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Offset from the Gaussian centre to the pixel centre (fi, fj are the integer pixel indices).
+__device__ __forceinline__ void pixel_offset(float fi, float fj, float fc, float4 pos, float& dx, float& dy) {
+    dx = __fsub_rn(__fsub_rn(fi, fc), pos.z);
+    dy = __fsub_rn(__fsub_rn(fj, pos.y), pos.w);
+}
+
+// Base-2 exponent of alpha before the clamp: log2(o) - 0.5 log2(e) d^T conic d (Eq. 2).
+__device__ __forceinline__ float gauss_exponent(float4 con, float dx, float dy) {
+    float q = __fmaf_rn(con.x, dx, __fmul_rn(con.y, dy));
+    float r = __fmaf_rn(__fmul_rn(con.z, dy), dy, con.w);
+    return __fmaf_rn(q, dx, r);
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+}  // namespace odgs

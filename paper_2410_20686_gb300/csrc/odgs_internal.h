@@ -1,0 +1,105 @@
+// Launcher interfaces between the C-ABI host code (api.cu) and the kernel files.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "odgs_common.cuh"
+
+namespace odgs {
+
+struct ViewTable {
+    ViewDev v[kMaxViews];
+    int n_views;
+    uint32_t n_items;
+};
+
+struct PreArgs {
+    const float *means, *scales, *quats, *opacity, *sh;
+    int n, n_views, sh_coeffs;
+    const ViewDev* views;
+    const float4* trig;
+    Settings st;
+    float4 *rec_a, *rec_b, *rec_c;
+    uint2* rect;
+    uint32_t *dkey, *dval;
+    Header* hdr;
+};
+
+struct PreBwdArgs {
+    const float *means, *scales, *quats, *opacity, *sh;
+    int n, n_views, sh_coeffs;
+    const ViewDev* views;
+    float dilation;
+    const float4* acc;
+    float *g_means, *g_scales, *g_quats, *g_opacity, *g_sh;
+    int accumulate;
+};
+
+struct BinArgs {
+    const uint32_t* sorted_idx;
+    const uint2* rect;
+    const ViewDev* views;
+    int n_per_view;
+    uint32_t n_items;
+    unsigned long long* block_sums;
+    Header* hdr;
+    unsigned long long capacity;
+    uint32_t *keys, *vals;
+};
+
+struct FwdArgs {
+    const ViewDev* views;
+    int n_views, total_tiles, tile_w, tile_h, batch;
+    uint32_t n_items;
+    const uint2* ranges;
+    const uint32_t* pair_vals;
+    const float4 *rec_a, *rec_b, *rec_c;
+    float* images[kMaxViews];
+    float* user_T[kMaxViews];
+    float* T_final;
+    uint32_t* n_last;
+    float bg[3];
+    Header* hdr;
+};
+
+struct BwdArgs {
+    const ViewDev* views;
+    int n_views, total_tiles, tile_w, tile_h, batch;
+    uint32_t n_items;
+    const uint2* ranges;
+    const uint32_t* pair_vals;
+    const float4 *rec_a, *rec_b, *rec_c;
+    const float* dL_dimages[kMaxViews];
+    const float* T_final;
+    const uint32_t* n_last;
+    float bg[3];
+    float4* acc;
+    Header* hdr;
+};
+
+cudaError_t launch_setup(const ViewTable& tab, ViewDev* views, float4* trig, Header* hdr, int total_trig,
+                         cudaStream_t st);
+cudaError_t launch_preprocess(const PreArgs& a, int sh_degree, cudaStream_t st);
+cudaError_t launch_preprocess_bwd(const PreBwdArgs& a, int sh_degree, cudaStream_t st);
+
+int radix_passes(int bits);
+size_t radix_lookback_words(size_t max_items);
+cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
+                              uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
+                              cudaStream_t st, int* result_buf, int* launches);
+
+int scan_blocks_for(uint32_t n_items);
+cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches);
+cudaError_t launch_tile_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges, int total_tiles,
+                               size_t max_pairs, int num_sms, cudaStream_t st, int* launches);
+
+size_t render_fwd_smem(int batch);
+size_t render_bwd_smem(int batch, int threads);
+int render_fwd_occupancy(int threads, int batch);
+int render_bwd_occupancy(int threads, int batch);
+cudaError_t launch_render_fwd(const FwdArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_render_bwd(const BwdArgs& a, int grid, cudaStream_t st);
+
+}  // namespace odgs

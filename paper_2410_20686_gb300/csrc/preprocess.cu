@@ -1,0 +1,585 @@
+// Per-Gaussian kernels of the ODGS ERP rasterizer (sm_103a):
+//   k_setup          per-view tables (pixel-centre cos/sin in float-float), header reset
+//   k_preprocess     forward projection per (Gaussian, view): Sec. 3.1-3.2, Eq. 4-8
+//   k_preprocess_bwd chain rule from screen-space gradients to the parameters: App. A.3
+// Both per-Gaussian kernels read each Gaussian's parameters once and loop over the views in
+// registers, so a batch of V views costs one parameter read (HBM-bound for SH degree 3).
+#include "odgs_common.cuh"
+#include "odgs_internal.h"
+
+namespace odgs {
+
+// ------------------------------------------------------------------ setup
+
+__global__ void k_setup(ViewTable tab, ViewDev* views, float4* trig, Header* hdr, int total_trig) {
+    int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < tab.n_views) views[gid] = tab.v[gid];
+    if (gid == 0) {
+        hdr->pairs = 0ull;
+        hdr->pairs_emitted = 0ull;
+        hdr->evals_fwd = 0ull;
+        hdr->evals_bwd = 0ull;
+        hdr->blended = 0ull;
+        hdr->status = 0u;
+        hdr->n_items = tab.n_items;
+        hdr->n_pairs_sort = 0u;
+        hdr->work_fwd = 0u;
+        hdr->work_bwd = 0u;
+    }
+    for (int e = gid; e < total_trig; e += gridDim.x * blockDim.x) {
+        // locate the view and whether e is a column or a row entry
+        int v = 0;
+        while (v + 1 < tab.n_views && tab.v[v + 1].trig_u <= e) ++v;
+        const ViewDev& V = tab.v[v];
+        double c, s;
+        if (e < V.trig_v) {
+            // column centre azimuth phi0 = 2 pi (c0 + 0.5) / W - pi   (inverse of Eq. 4)
+            int col = e - V.trig_u;
+            sincospi(2.0 * (col + 0.5) / V.W - 1.0, &s, &c);
+        } else {
+            // row centre elevation theta0 = pi / 2 - pi (r0 + 0.5) / H  (inverse of Eq. 4)
+            int row = e - V.trig_v;
+            sincospi(0.5 - (row + 0.5) / V.H, &s, &c);
+        }
+        float ch = (float)c, sh = (float)s;
+        trig[e] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+    }
+}
+
+// ------------------------------------------------------------------ shared math
+
+// Rotation matrix of the normalized quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Real SH basis (orthonormal, no Condon-Shortley phase) as Cartesian polynomials of the unit
+// direction (x, y, z); index l^2 + l + m.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+    Y[0] = 0.28209479177387814f;
+    if (DEG >= 1) {
+        const float c1 = 0.4886025119029199f;
+        Y[1] = c1 * y; Y[2] = c1 * z; Y[3] = c1 * x;
+    }
+    if (DEG >= 2) {
+        const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.5462742152960396f;
+        Y[4] = a * x * y; Y[5] = a * y * z; Y[6] = b * (3.f * z * z - 1.f); Y[7] = a * x * z;
+        Y[8] = c * (x * x - y * y);
+    }
+    if (DEG >= 3) {
+        const float a = 0.5900435899266435f, b = 2.890611442640554f, c = 0.4570457994644658f,
+                    d = 0.3731763325901154f, e = 1.445305721320277f;
+        Y[9] = a * y * (3.f * x * x - y * y);
+        Y[10] = b * x * y * z;
+        Y[11] = c * y * (5.f * z * z - 1.f);
+        Y[12] = d * z * (5.f * z * z - 3.f);
+        Y[13] = c * x * (5.f * z * z - 1.f);
+        Y[14] = e * z * (x * x - y * y);
+        Y[15] = a * x * (x * x - 3.f * y * y);
+    }
+}
+
+// Gradient of the polynomials above w.r.t. (x, y, z), accumulated as sum_k w_k grad Y_k.
+template <int DEG>
+__device__ __forceinline__ void sh_grad_acc(float x, float y, float z, const float w[16], float& gx, float& gy,
+                                            float& gz) {
+    gx = gy = gz = 0.f;
+    if (DEG >= 1) {
+        const float c1 = 0.4886025119029199f;
+        gy += c1 * w[1]; gz += c1 * w[2]; gx += c1 * w[3];
+    }
+    if (DEG >= 2) {
+        const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.5462742152960396f;
+        gx += a * y * w[4]; gy += a * x * w[4];
+        gy += a * z * w[5]; gz += a * y * w[5];
+        gz += 6.f * b * z * w[6];
+        gx += a * z * w[7]; gz += a * x * w[7];
+        gx += 2.f * c * x * w[8]; gy -= 2.f * c * y * w[8];
+    }
+    if (DEG >= 3) {
+        const float a = 0.5900435899266435f, b = 2.890611442640554f, c = 0.4570457994644658f,
+                    d = 0.3731763325901154f, e = 1.445305721320277f;
+        gx += 6.f * a * x * y * w[9]; gy += 3.f * a * (x * x - y * y) * w[9];
+        gx += b * y * z * w[10]; gy += b * x * z * w[10]; gz += b * x * y * w[10];
+        gy += c * (5.f * z * z - 1.f) * w[11]; gz += 10.f * c * y * z * w[11];
+        gz += d * (15.f * z * z - 3.f) * w[12];
+        gx += c * (5.f * z * z - 1.f) * w[13]; gz += 10.f * c * x * z * w[13];
+        gx += 2.f * e * x * z * w[14]; gy -= 2.f * e * y * z * w[14]; gz += e * (x * x - y * y) * w[14];
+        gx += 3.f * a * (x * x - y * y) * w[15]; gy -= 6.f * a * x * y * w[15];
+    }
+}
+
+// Radial depth in IEEE single precision with the fixed operation order of the depth key:
+// t_i = ((R_i0 m0 + R_i1 m1) + R_i2 m2) + t_i, r = sqrt((tx tx + ty ty) + tz tz).
+__device__ __forceinline__ float depth_key(const ViewDev& V, float m0, float m1, float m2) {
+    float t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float s = __fadd_rn(__fmul_rn(V.R[3 * i], m0), __fmul_rn(V.R[3 * i + 1], m1));
+        s = __fadd_rn(s, __fmul_rn(V.R[3 * i + 2], m2));
+        t[i] = __fadd_rn(s, V.t[i]);
+    }
+    float q = __fadd_rn(__fmul_rn(t[0], t[0]), __fmul_rn(t[1], t[1]));
+    q = __fadd_rn(q, __fmul_rn(t[2], t[2]));
+    return __fsqrt_rn(q);
+}
+
+// J_omni (Eq. 8) from the camera-space mean, written with sec(theta) = r / rho,
+// cos(phi) = tz / rho, sin(phi) = tx / rho, sin(theta) = -ty / r, cos(theta) = rho / r:
+//   row 1 = fx [tz, 0, -tx] / rho^2,  row 2 = fy [-tx ty / rho, rho, -ty tz / rho] / r^2.
+struct JGeom {
+    float J[6];
+    float rho, rho2, r2;
+};
+__device__ __forceinline__ JGeom omni_jacobian(float tx, float ty, float tz, float fx, float fy) {
+    JGeom g;
+    g.rho2 = tx * tx + tz * tz;
+    g.rho = sqrtf(g.rho2);
+    g.r2 = g.rho2 + ty * ty;
+    float a = fx / g.rho2;
+    float b = fy / (g.r2 * g.rho);
+    g.J[0] = a * tz; g.J[1] = 0.f; g.J[2] = -a * tx;
+    g.J[3] = -b * tx * ty; g.J[4] = fy * g.rho / g.r2; g.J[5] = -b * ty * tz;
+    return g;
+}
+
+// TM = (J W) M, the 2x3 factor of Sigma_2D = TM TM^T (+ dilation).
+__device__ __forceinline__ void tm_factor(const float J[6], const float W[9], const float M[9], float T[6],
+                                          float TM[6]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            T[3 * i + k] = J[3 * i] * W[k] + J[3 * i + 1] * W[3 + k] + J[3 * i + 2] * W[6 + k];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            TM[3 * i + k] = T[3 * i] * M[k] + T[3 * i + 1] * M[3 + k] + T[3 * i + 2] * M[6 + k];
+}
+
+// Sigma_2D = TM TM^T + delta I and its determinant without cancellation:
+// det(TM TM^T) = |TM_1 x TM_2|^2 (Lagrange's identity).
+struct Cov2 {
+    float A, B, C, det, A0, C0;
+};
+__device__ __forceinline__ Cov2 cov2d(const float TM[6], float delta) {
+    Cov2 c;
+    c.A0 = TM[0] * TM[0] + TM[1] * TM[1] + TM[2] * TM[2];
+    c.C0 = TM[3] * TM[3] + TM[4] * TM[4] + TM[5] * TM[5];
+    c.B = TM[0] * TM[3] + TM[1] * TM[4] + TM[2] * TM[5];
+    float cx = TM[1] * TM[5] - TM[2] * TM[4];
+    float cy = TM[2] * TM[3] - TM[0] * TM[5];
+    float cz = TM[0] * TM[4] - TM[1] * TM[3];
+    float det0 = cx * cx + cy * cy + cz * cz;
+    c.A = c.A0 + delta;
+    c.C = c.C0 + delta;
+    c.det = det0 + delta * (c.A0 + c.C0) + delta * delta;
+    return c;
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float* __restrict__ sh, int stride, int g, float c[16][3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float* p = sh + (size_t)g * stride * 3;
+    if ((stride * 3) % 4 == 0) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        float tmp[((K * 3 + 3) / 4) * 4];
+#pragma unroll
+        for (int i = 0; i < (K * 3 + 3) / 4; ++i) {
+            float4 q = __ldg(p4 + i);
+            tmp[4 * i] = q.x; tmp[4 * i + 1] = q.y; tmp[4 * i + 2] = q.z; tmp[4 * i + 3] = q.w;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) c[k][ch] = tmp[3 * k + ch];
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) c[k][ch] = __ldg(p + 3 * k + ch);
+    }
+}
+
+// ------------------------------------------------------------------ forward projection
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long local_pairs = 0ull;
+    if (g < a.n) {
+        const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
+        const float s0 = __ldg(a.scales + 3 * g), s1 = __ldg(a.scales + 3 * g + 1), s2 = __ldg(a.scales + 3 * g + 2);
+        const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
+        const float o = __ldg(a.opacity + g);
+        float shc[16][3];
+        load_sh<DEG>(a.sh, a.sh_coeffs, g, shc);
+
+        // Sigma = M M^T with M = R(q) S (Sec. 3.1)
+        float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        float Rq[9], M[9];
+        quat_rot(q.x / qn, q.y / qn, q.z / qn, q.w / qn, Rq);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            M[3 * i] = Rq[3 * i] * s0; M[3 * i + 1] = Rq[3 * i + 1] * s1; M[3 * i + 2] = Rq[3 * i + 2] * s2;
+        }
+        const float Qalpha = (255.f * o > 1.f) ? 2.f * logf(255.f * o) : -1.f;  // Mahalanobis^2 at alpha = 1/255
+        const float Qb = Qalpha * (1.f + 1e-4f) + 1e-4f;
+
+        for (int v = 0; v < a.n_views; ++v) {
+            const ViewDev& V = a.views[v];
+            const size_t item = (size_t)v * a.n + g;
+            uint2 rect = make_uint2(0u, 0u);
+            uint32_t key = 0xFFFFFFFFu;
+            const float r = depth_key(V, m0, m1, m2);
+            bool ok = (r > a.st.r_near) && (r < a.st.r_far) && (Qalpha > 0.f);
+            // camera-space mean in float-float: t = W mu + t_wc
+            ff t[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                ff acc = ff_add(two_prod(V.R[3 * i], m0), two_prod(V.R[3 * i + 1], m1));
+                acc = ff_add(acc, two_prod(V.R[3 * i + 2], m2));
+                t[i] = ff_add(acc, ff{V.t[i], 0.f});
+            }
+            const float tx = t[0].hi, ty = t[1].hi, tz = t[2].hi;
+            JGeom jg = omni_jacobian(tx, ty, tz, V.fx, V.fy);
+            ok = ok && (jg.rho > 1e-4f * r);  // too close to a pole: sec(theta) > 1e4
+            if (ok) {
+                // ERP mean (Eq. 4) as pixel anchor + offset: rotate (t_x, t_z) by minus the
+                // azimuth of the anchor column's centre, then the elevation likewise.
+                float ua = atan2f(tx, tz) * V.fx + 0.5f * V.W;
+                int c0 = min(max((int)floorf(ua), 0), V.W - 1);
+                float4 tu = a.trig[V.trig_u + c0];
+                ff cph{tu.x, tu.y}, sph{tu.z, tu.w};
+                ff ar = ff_add(ff_mul(t[0], cph), ff_neg(ff_mul(t[2], sph)));  // rho sin(phi - phi0)
+                ff br = ff_add(ff_mul(t[0], sph), ff_mul(t[2], cph));          // rho cos(phi - phi0)
+                float du = atan2f(ar.hi, br.hi) * V.fx;
+                ff rho = ff_sqrt(ff_add(ff_mul(ar, ar), ff_mul(br, br)));
+                ff ny = ff_neg(t[1]);
+                float va = -atan2f(ny.hi, rho.hi) * V.fy + 0.5f * V.H;
+                int r0 = min(max((int)floorf(va), 0), V.H - 1);
+                float4 tv = a.trig[V.trig_v + r0];
+                ff cth{tv.x, tv.y}, sth{tv.z, tv.w};
+                ff ae = ff_add(ff_mul(ny, cth), ff_neg(ff_mul(rho, sth)));  // r sin(theta - theta0)
+                ff be = ff_add(ff_mul(rho, cth), ff_mul(ny, sth));          // r cos(theta - theta0)
+                float dv = -atan2f(ae.hi, be.hi) * V.fy;
+
+                // Sigma_2D = (J W M)(J W M)^T + delta I  (Eq. 8 and Sec. 3.1)
+                float T[6], TM[6];
+                tm_factor(jg.J, V.R, M, T, TM);
+                Cov2 c2 = cov2d(TM, a.st.dilation);
+                ok = c2.det > 0.f;
+                if (ok) {
+                    float inv = 1.f / c2.det;
+                    float ca = c2.C * inv, cb = -c2.B * inv, cc = c2.A * inv;
+                    // conservative pixel rectangle of {alpha >= 1/255}; seam wrap in u
+                    float eu = sqrtf(Qb * c2.A), ev = sqrtf(Qb * c2.C);
+                    uint32_t tx0, ntx;
+                    const int tw = a.st.tile_w, th = a.st.tile_h;
+                    bool allcols = eu >= (float)V.W;
+                    if (!allcols) {
+                        int ilo = c0 + (int)ceilf(du - eu), ihi = c0 + (int)floorf(du + eu);
+                        if (ihi < ilo) ok = false;
+                        allcols = ihi - ilo + 1 >= V.W;
+                        int tlo = floor_div(ilo, tw), thi = floor_div(ihi, tw);
+                        int n = thi - tlo + 1;
+                        if (n >= V.tiles_x) allcols = true;
+                        ntx = (uint32_t)n;
+                        tx0 = (uint32_t)(((tlo % V.tiles_x) + V.tiles_x) % V.tiles_x);
+                    }
+                    if (allcols) { tx0 = 0u; ntx = (uint32_t)V.tiles_x; }
+                    ev = fminf(ev, 2.f * V.H);
+                    int jlo = max(0, r0 + (int)ceilf(dv - ev)), jhi = min(V.H - 1, r0 + (int)floorf(dv + ev));
+                    if (jhi < jlo) ok = false;
+                    if (ok) {
+                        uint32_t ty0 = (uint32_t)(jlo / th), nty = (uint32_t)(jhi / th) - ty0 + 1u;
+                        rect = make_uint2(tx0 | (ntx << 16), ty0 | (nty << 16));
+                        local_pairs += (unsigned long long)ntx * nty;
+                        key = __float_as_uint(r);
+                        // view-dependent colour: max(0, sum_k sh_k Y_k(d) + 0.5), d from the
+                        // camera centre to the mean in world space
+                        float dx = m0 - V.cam[0], dy = m1 - V.cam[1], dz = m2 - V.cam[2];
+                        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+                        float Y[16];
+                        sh_basis<DEG>(dx * il, dy * il, dz * il, Y);
+                        float rgb[3];
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            float acc = 0.5f;
+#pragma unroll
+                            for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
+                            rgb[ch] = fmaxf(acc, 0.f);
+                        }
+                        a.rec_a[item] = make_float4(du, dv, __uint_as_float((uint32_t)c0 | ((uint32_t)r0 << 16)), o);
+                        a.rec_b[item] = make_float4(ca, cb, cc, 0.f);
+                        a.rec_c[item] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+                    }
+                }
+            }
+            a.rect[item] = rect;
+            a.dkey[item] = key;
+            a.dval[item] = (uint32_t)item;
+        }
+    }
+    // frame pair count
+    for (int off = 16; off > 0; off >>= 1) local_pairs += __shfl_xor_sync(0xffffffffu, local_pairs, off);
+    __shared__ unsigned long long s_sum[8];
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = local_pairs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_sum[w];
+        if (tot) atomicAdd(&a.hdr->pairs, tot);
+    }
+}
+
+// ------------------------------------------------------------------ backward chain rule
+
+template <int DEG>
+__global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
+    const float s[3] = {__ldg(a.scales + 3 * g), __ldg(a.scales + 3 * g + 1), __ldg(a.scales + 3 * g + 2)};
+    const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
+
+    float gm[3] = {0.f, 0.f, 0.f}, gop = 0.f;
+    float gsh[16][3];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+    float dM[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dM[i] = 0.f;
+
+    float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
+    float Rq[9], M[9];
+    quat_rot(qw, qx, qy, qz, Rq);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = Rq[3 * i + j] * s[j];
+
+    bool any = false;
+    bool sh_loaded = false;
+    float shc[16][3];
+    for (int v = 0; v < a.n_views; ++v) {
+        const size_t item = (size_t)v * a.n + g;
+        const float4 g0 = a.acc[3 * item], g1 = a.acc[3 * item + 1], g2 = a.acc[3 * item + 2];
+        // accumulator layout: (du, dv, da, db), (dc, dopacity, dr, dg), (db, 0, 0, 0)
+        if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
+            g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
+            continue;
+        any = true;
+        const ViewDev& V = a.views[v];
+        const float* W = V.R;
+        float t[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) t[i] = W[3 * i] * m0 + W[3 * i + 1] * m1 + W[3 * i + 2] * m2 + V.t[i];
+        const float tx = t[0], ty = t[1], tz = t[2];
+        JGeom jg = omni_jacobian(tx, ty, tz, V.fx, V.fy);
+        float T[6], TM[6];
+        tm_factor(jg.J, W, M, T, TM);
+        Cov2 c2 = cov2d(TM, a.dilation);
+        const float D = c2.det, iD2 = 1.f / (D * D);
+        const float A = c2.A, B = c2.B, C = c2.C;
+        const float da = g0.z, db = g0.w, dc = g1.x;
+        // conic (C, -B, A) / D -> Sigma_2D, with B the single off-diagonal variable
+        const float dA = (-C * C * da + B * C * db - B * B * dc) * iD2;
+        const float dB = (2.f * B * C * da - (A * C + B * B) * db + 2.f * A * B * dc) * iD2;
+        const float dC = (-B * B * da + A * B * db - A * A * dc) * iD2;
+        // Sigma_2D = TM TM^T: d/dTM_1 = 2 dA TM_1 + dB TM_2, d/dTM_2 = 2 dC TM_2 + dB TM_1
+        float dTM[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dTM[k] = 2.f * dA * TM[k] + dB * TM[3 + k];
+            dTM[3 + k] = 2.f * dC * TM[3 + k] + dB * TM[k];
+        }
+        // TM = T M: dT = dTM M^T, dM += T^T dTM
+        float dT[6];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dT[3 * i + j] = dTM[3 * i] * M[3 * j] + dTM[3 * i + 1] * M[3 * j + 1] + dTM[3 * i + 2] * M[3 * j + 2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dM[3 * j + k] += T[j] * dTM[k] + T[3 + j] * dTM[3 + k];
+        // T = J W: dJ = dT W^T
+        float dJ[6];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dJ[3 * i + j] = dT[3 * i] * W[3 * j] + dT[3 * i + 1] * W[3 * j + 1] + dT[3 * i + 2] * W[3 * j + 2];
+        // dL/dt: mean path d(u, v)/dt = J_omni (Eq. 10) plus J_omni's dependence on t
+        const float fx = V.fx, fy = V.fy;
+        const float rho = jg.rho, rho2 = jg.rho2, r2 = jg.r2;
+        const float irho4 = 1.f / (rho2 * rho2);
+        const float ir4 = 1.f / (r2 * r2);
+        const float irho = 1.f / rho, irho3 = irho / rho2;
+        float dtx = jg.J[0] * g0.x + jg.J[3] * g0.y;
+        float dty = jg.J[4] * g0.y;
+        float dtz = jg.J[2] * g0.x + jg.J[5] * g0.y;
+        // row 1: J11 = fx tz / rho^2, J13 = -fx tx / rho^2
+        dtx += fx * irho4 * (-2.f * tx * tz * dJ[0] + (tx * tx - tz * tz) * dJ[2]);
+        dtz += fx * irho4 * ((tx * tx - tz * tz) * dJ[0] + 2.f * tx * tz * dJ[2]);
+        // row 2: J21 = -fy tx ty / (r^2 rho), J22 = fy rho / r^2, J23 = -fy ty tz / (r^2 rho)
+        const float k3 = fy * ir4 * irho3, k1 = fy * ir4 * irho;
+        const float rr = 2.f * rho2 + r2;
+        dtx += -k3 * ty * (tz * tz * r2 - 2.f * tx * tx * rho2) * dJ[3];
+        dty += -k1 * tx * (r2 - 2.f * ty * ty) * dJ[3];
+        dtz += k3 * tx * ty * tz * rr * dJ[3];
+        dtx += k1 * tx * (r2 - 2.f * rho2) * dJ[4];
+        dty += -2.f * fy * ir4 * rho * ty * dJ[4];
+        dtz += k1 * tz * (r2 - 2.f * rho2) * dJ[4];
+        dtx += k3 * tx * ty * tz * rr * dJ[5];
+        dty += -k1 * tz * (r2 - 2.f * ty * ty) * dJ[5];
+        dtz += -k3 * ty * (tx * tx * r2 - 2.f * tz * tz * rho2) * dJ[5];
+        // t = W mu + t_wc
+        gm[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
+        gm[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
+        gm[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+        gop += g1.y;
+
+        // colour
+        if (!sh_loaded) { load_sh<DEG>(a.sh, a.sh_coeffs, g, shc); sh_loaded = true; }
+        const float vx = m0 - V.cam[0], vy = m1 - V.cam[1], vz = m2 - V.cam[2];
+        const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+        const float x = vx * il, y = vy * il, z = vz * il;
+        float Y[16];
+        sh_basis<DEG>(x, y, z, Y);
+        const float drgb[3] = {g1.z, g1.w, g2.x};
+        float wsum[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
+            if (acc < 0.f) continue;  // clamped channel
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                gsh[k][ch] += drgb[ch] * Y[k];
+                wsum[k] += drgb[ch] * shc[k][ch];
+            }
+        }
+        if (DEG > 0) {
+            float gx, gy, gz;
+            sh_grad_acc<DEG>(x, y, z, wsum, gx, gy, gz);
+            const float dd = gx * x + gy * y + gz * z;  // project out the radial part
+            gm[0] += (gx - dd * x) * il;
+            gm[1] += (gy - dd * y) * il;
+            gm[2] += (gz - dd * z) * il;
+        }
+    }
+
+    float gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+    if (any) {
+        // M = R diag(s): ds_j = sum_i dM_ij R_ij, dR_ij = dM_ij s_j
+        float dR[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gs[j] += dM[3 * i + j] * Rq[3 * i + j];
+                dR[3 * i + j] = dM[3 * i + j] * s[j];
+            }
+        // R(q) partials (q normalized)
+        float dw = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+        float dx = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - qw * dR[5] + qz * dR[6] +
+                          qw * dR[7] - 2.f * qx * dR[8]);
+        float dy = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] +
+                          qz * dR[7] - 2.f * qy * dR[8]);
+        float dz = 2.f * (-2.f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.f * qz * dR[4] +
+                          qy * dR[5] + qx * dR[6] + qy * dR[7]);
+        float dot = qw * dw + qx * dx + qy * dy + qz * dz;
+        gq[0] = (dw - qw * dot) / qn; gq[1] = (dx - qx * dot) / qn;
+        gq[2] = (dy - qy * dot) / qn; gq[3] = (dz - qz * dot) / qn;
+    }
+    // write (or accumulate) the parameter gradients
+    float* pm = a.g_means + 3 * g;
+    float* ps = a.g_scales + 3 * g;
+    float* pq = a.g_quats + 4 * g;
+    float* psh = a.g_sh + (size_t)g * a.sh_coeffs * 3;
+    if (a.accumulate) {
+        if (!any) return;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { pm[i] += gm[i]; ps[i] += gs[i]; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pq[i] += gq[i];
+        a.g_opacity[g] += gop;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] += gsh[k][ch];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { pm[i] = gm[i]; ps[i] = gs[i]; }
+        reinterpret_cast<float4*>(pq)[0] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        a.g_opacity[g] = gop;
+        if ((a.sh_coeffs * 3) % 4 == 0 && (K * 3) % 4 == 0) {
+            float4* p4 = reinterpret_cast<float4*>(psh);
+#pragma unroll
+            for (int i = 0; i < K * 3 / 4; ++i) {
+                const int e = 4 * i;
+                p4[i] = make_float4(gsh[e / 3][e % 3], gsh[(e + 1) / 3][(e + 1) % 3], gsh[(e + 2) / 3][(e + 2) % 3],
+                                    gsh[(e + 3) / 3][(e + 3) % 3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] = gsh[k][ch];
+        }
+        for (int k = K; k < a.sh_coeffs; ++k)
+            for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] = 0.f;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t launch_setup(const ViewTable& tab, ViewDev* views, float4* trig, Header* hdr, int total_trig,
+                         cudaStream_t st) {
+    int threads = 256;
+    int blocks = (max(total_trig, tab.n_views) + threads - 1) / threads;
+    blocks = max(1, min(blocks, 1024));
+    k_setup<<<blocks, threads, 0, st>>>(tab, views, trig, hdr, total_trig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const PreArgs& a, int sh_degree, cudaStream_t st) {
+    if (a.n == 0) return cudaSuccess;
+    int threads = 256, blocks = (a.n + threads - 1) / threads;
+    switch (sh_degree) {
+        case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(a); break;
+        case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(a); break;
+        case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(a); break;
+        default: k_preprocess<3><<<blocks, threads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const PreBwdArgs& a, int sh_degree, cudaStream_t st) {
+    if (a.n == 0) return cudaSuccess;
+    int threads = 128, blocks = (a.n + threads - 1) / threads;
+    switch (sh_degree) {
+        case 0: k_preprocess_bwd<0><<<blocks, threads, 0, st>>>(a); break;
+        case 1: k_preprocess_bwd<1><<<blocks, threads, 0, st>>>(a); break;
+        case 2: k_preprocess_bwd<2><<<blocks, threads, 0, st>>>(a); break;
+        default: k_preprocess_bwd<3><<<blocks, threads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace odgs

@@ -1,0 +1,237 @@
+// Stable LSD radix sort of 32-bit keys with 32-bit values (sm_103a), used twice per frame:
+//   1. (view, Gaussian) items by the bits of their FP32 radial depth   ("sorting by depth",
+//      Sec. 3.1), ties kept in item order;
+//   2. the (tile, Gaussian) pairs, emitted in depth order, by tile id.
+// Together they give every tile its Gaussians in (depth, index) order, the same order as one
+// stable sort of 64-bit (tile | depth) keys, with far fewer bytes moved.
+//
+// One histogram kernel counts the digits of all passes in a single read of the keys; each
+// pass is then one "onesweep" kernel (Adinets & Merrill 2022): a CTA ranks a 4096-key tile in
+// shared memory (warp-level match ranking keeps it stable), publishes its per-digit counts,
+// obtains the exclusive prefix of all earlier tiles by decoupled look-back, and writes its keys
+// digit-run by digit-run (coalesced). Look-back waits are bounded: a CTA that gives up sets
+// kStTimeout in the status word and returns.
+#include "odgs_common.cuh"
+#include "odgs_internal.h"
+
+namespace odgs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kRadix = 256;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
+                                                    int begin_bit, int n_passes, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[4][kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    const uint32_t n = *n_ptr;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    // warp-uniform trip count so every lane takes part in the match
+    for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
+        const uint32_t idx = base + lane;
+        const bool valid = idx < n;
+        const uint32_t k = valid ? keys[idx] : 0u;
+        for (int p = 0; p < n_passes; ++p) {
+            const uint32_t d = (k >> (begin_bit + 8 * p)) & 0xFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+            if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_passes * kRadix; i += blockDim.x) {
+        uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < kSortWarps; ++i) {
+        uint32_t s = s_warp[i];
+        if (i < w) wpre += s;
+        tot += s;
+    }
+    total = tot;
+    __syncthreads();
+    return wpre + x - v;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         const uint32_t* __restrict__ n_ptr, int shift,
+                                                         int bits, const uint32_t* __restrict__ hist,
+                                                         uint32_t* lookback, uint32_t* tile_ctr, uint32_t* status) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_warp_hist[kSortWarps][kRadix];
+    __shared__ uint32_t s_digit_excl[kRadix];
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_keys[kSortThreads * kSortItems];
+    __shared__ uint32_t s_vals[kSortThreads * kSortItems];
+    __shared__ uint32_t s_scan[kSortWarps];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0u;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t n = *n_ptr;
+    const uint32_t base = tile * (uint32_t)(kSortThreads * kSortItems);
+    if (base >= n) return;  // CTA-uniform
+    const uint32_t mask = (1u << bits) - 1u;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    const uint32_t wbase = base + (uint32_t)warp * (32u * kSortItems);
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
+        const bool valid = idx < n;
+        key[i] = valid ? kin[idx] : 0u;
+        val[i] = valid ? vin[idx] : 0u;
+    }
+    // stable warp-level ranking: items are ordered by (warp, i, lane)
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
+        const bool valid = idx < n;
+        const uint32_t d = (key[i] >> shift) & mask;
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        const uint32_t before = valid ? s_warp_hist[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) s_warp_hist[warp][d] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+        rank[i] = before + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit (one thread each): exclusive prefix over warps, CTA count
+    uint32_t cnt = 0;
+    {
+        const int d = tid;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t c = s_warp_hist[w][d];
+            s_warp_hist[w][d] = cnt;
+            cnt += c;
+        }
+    }
+    // publish this tile's count for digit tid
+    uint32_t* my = lookback + (size_t)tile * kRadix + tid;
+    if (tile == 0) {
+        atomicExch(my, kFlagPrefix | cnt);
+    } else {
+        atomicExch(my, kFlagAgg | cnt);
+    }
+    uint32_t tot;
+    const uint32_t dex = block_excl_scan_256(cnt, s_scan, tot);
+    s_digit_excl[tid] = dex;
+    // global digit offset of this pass (exclusive scan of the global histogram)
+    const uint32_t g = hist[tid];
+    const uint32_t gex = block_excl_scan_256(g, s_scan, tot);
+    // decoupled look-back for digit tid
+    uint32_t excl = 0;
+    if (tile > 0) {
+        int j = (int)tile - 1;
+        uint32_t spins = 0;
+        while (j >= 0) {
+            const uint32_t e = ld_volatile(lookback + (size_t)j * kRadix + tid);
+            const uint32_t flag = e & ~kCountMask;
+            if (flag == 0u) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(status, kStTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            excl += e & kCountMask;
+            if (flag == kFlagPrefix) break;
+            --j;
+        }
+        atomicExch(my, kFlagPrefix | (excl + cnt));
+    }
+    s_base[tid] = gex + excl - dex;
+    __syncthreads();
+    // scatter into shared memory in sorted order within the tile
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
+        if (idx < n) {
+            const uint32_t d = (key[i] >> shift) & mask;
+            const uint32_t pos = s_digit_excl[d] + s_warp_hist[warp][d] + rank[i];
+            s_keys[pos] = key[i];
+            s_vals[pos] = val[i];
+        }
+    }
+    __syncthreads();
+    const uint32_t count = min((uint32_t)(kSortThreads * kSortItems), n - base);
+    for (uint32_t p = tid; p < count; p += kSortThreads) {
+        const uint32_t k = s_keys[p];
+        const uint32_t d = (k >> shift) & mask;
+        const uint32_t dst = s_base[d] + p;
+        if (dst < n) {  // only false after a look-back that gave up (status already set)
+            kout[dst] = k;
+            vout[dst] = s_vals[p];
+        }
+    }
+}
+
+int radix_passes(int bits) { return (bits + 7) / 8; }
+
+size_t radix_lookback_words(size_t max_items) {
+    size_t tiles = (max_items + kSortThreads * kSortItems - 1) / (kSortThreads * kSortItems);
+    return (tiles ? tiles : 1) * kRadix;
+}
+
+// Sorts (k[0], v[0]) by key bits [0, bits); returns the buffer index (0 or 1) that holds the
+// result. scratch: hist [4 * 256] + tile counters [4] + lookback [radix_lookback_words].
+cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
+                              uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
+                              cudaStream_t st, int* result_buf, int* launches) {
+    const int passes = radix_passes(bits);
+    *result_buf = 0;
+    if (passes == 0 || max_items == 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * kRadix, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(tile_ctrs, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return e;
+    int hblocks = (int)min((max_items + 255) / 256, (size_t)num_sms * 8);
+    hblocks = max(hblocks, 1);
+    k_radix_hist<<<hblocks, 256, 0, st>>>(k[0], n_ptr, 0, passes, hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *launches += 1;
+    const size_t lb_words = radix_lookback_words(max_items);
+    const int tiles = (int)(lb_words / kRadix);
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        const int pbits = min(8, bits - shift);
+        if ((e = cudaMemsetAsync(lookback, 0, sizeof(uint32_t) * lb_words, st)) != cudaSuccess) return e;
+        k_onesweep<<<tiles, kSortThreads, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits,
+                                                   hist + p * kRadix, lookback, tile_ctrs + p, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 1;
+        cur ^= 1;
+    }
+    *result_buf = cur;
+    return cudaSuccess;
+}
+
+}  // namespace odgs
