@@ -153,6 +153,25 @@ odgs_status odgs_frame_stats(odgs_ctx *ctx, odgs_stats *out, void *stream);
 /* Synchronizes the stream and returns the device status bits (ODGS_DEV_*) in *bits. */
 odgs_status odgs_get_status(odgs_ctx *ctx, uint32_t *bits, void *stream);
 
+/* Forward render of ONE view that allocates nothing and needs no workspace or pair buffer, for
+ * callers that cannot call cudaMalloc (a plugin or frame callback inside a host application that
+ * owns a fixed device-memory budget, or a real-time loop where cudaMalloc / cudaFree would
+ * synchronize the device). The paper has no counterpart: it is a packaging of the forward path
+ * (odgs_preprocess + odgs_bin_sort + odgs_render_fwd, same kernels, same image).
+ * Inputs: g, view, s (host structs; device arrays as for odgs_preprocess). Outputs: image
+ * [3][H][W] and final_T [H][W] (device, final_T may be NULL), and status_out (device, one
+ * uint32_t) which receives the device status bits (ODGS_DEV_CAPACITY when the frame had more
+ * pairs than fit) without a host synchronization.
+ * Scratch: a 32 MiB file-scope device array that every GPU using this library holds until the
+ * process exits. Limits: n <= 32768 Gaussians, W * H <= 524288 pixels, pairs up to what fits in
+ * the rest of the array (about 1.4 million); larger sizes return ODGS_ERR_INVALID_ARG and
+ * launch nothing. The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream capture. All calls
+ * share the array and each one resets the parts that must start at zero; calls whose work
+ * overlaps on the GPU (other streams, unordered host threads) race on it. */
+odgs_status odgs_render_fwd_static(const odgs_gaussians *g, const odgs_view *view, const odgs_settings *s,
+                                   float *image, float *final_T, uint32_t *status_out, void *stream);
+
 /* Kernel launches the last frame issued (for accounting). */
 int odgs_last_launch_count(const odgs_ctx *ctx);
 

@@ -21,7 +21,7 @@ MAX_VIEWS = 64
 EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buffer_size",
             "odgs_preprocess", "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd",
             "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
-            "odgs_last_launch_count", "odgs_status_string")
+            "odgs_render_fwd_static", "odgs_last_launch_count", "odgs_status_string")
 
 
 class OdgsError(RuntimeError):
@@ -82,13 +82,14 @@ def load(path: str = LIB_PATH):
     L.odgs_preprocess_bwd.argtypes = [vp, C.POINTER(Grads), vp]
     L.odgs_frame_stats.argtypes = [vp, C.POINTER(Stats), vp]
     L.odgs_get_status.argtypes = [vp, C.POINTER(C.c_uint32), vp]
+    L.odgs_render_fwd_static.argtypes = [C.POINTER(Gaussians), C.POINTER(View), C.POINTER(Settings), vp, vp, vp, vp]
     L.odgs_last_launch_count.argtypes = [vp]
     L.odgs_last_launch_count.restype = C.c_int
     L.odgs_status_string.argtypes = [C.c_int]
     L.odgs_status_string.restype = C.c_char_p
     for name in ("odgs_create", "odgs_workspace_size", "odgs_pair_buffer_size", "odgs_preprocess",
                  "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
-                 "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status"):
+                 "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
