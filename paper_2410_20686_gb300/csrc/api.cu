@@ -18,7 +18,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t hdr, views, trig, rec_a, rec_b, rec_c, rect, dkey0, dkey1, dval0, dval1, block_sums, ranges, T_final,
-        n_last, acc, sort_hist, sort_ctr, sort_lb, total;
+        n_last, acc, sort_hist, sort_ctr, sort_lb, big, total;
 };
 
 struct PairLayout {
@@ -57,6 +57,7 @@ Layout make_layout(size_t items, const Geometry& g) {
     L.sort_hist = take(sizeof(uint32_t) * 4 * 256);
     L.sort_ctr = take(sizeof(uint32_t) * 4);
     L.sort_lb = take(sizeof(uint32_t) * radix_lookback_words(items));
+    L.big = take(sizeof(uint2) * items);
     L.total = o;
     return L;
 }
@@ -332,6 +333,10 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     BinArgs b{};
     b.sorted_idx = dv[rb];
     b.rect = reinterpret_cast<const uint2*>(w + c->L.rect);
+    b.rec_a = reinterpret_cast<const float4*>(w + c->L.rec_a);
+    b.rec_b = reinterpret_cast<const float4*>(w + c->L.rec_b);
+    b.tile_w = c->s.tile_w;
+    b.tile_h = c->s.tile_h;
     b.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
     b.n_per_view = c->n > 0 ? c->n : 1;
     b.n_items = (uint32_t)c->geo.n_items;
@@ -340,6 +345,8 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     b.capacity = c->pb_cap;
     b.keys = pk[0];
     b.vals = pv[0];
+    b.big = reinterpret_cast<uint2*>(w + c->L.big);
+    b.num_sms = c->num_sms;
     if (launch_binning(b, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
     // 3. stable sort of the pairs by tile id
     int rp = 0;

@@ -5,8 +5,11 @@
 //                   depth order, at its exclusive-scan offset; pairs beyond the capacity are
 //                   dropped (status bit kStCapacity set by k_scan_blocks)
 //   k_tile_ranges   [start, end) of every tile's run in the tile-sorted pair list
-// A rectangle is tx0 | ntx << 16, ty0 | nty << 16; its columns wrap around the longitude seam
-// (tile column (tx0 + k) mod tiles_x).
+// An item's rect is (ty0 | nty << 16, number of tiles); the tiles of each of its tile rows are
+// recomputed from its records by band_columns (odgs_common.cuh), exactly as the preprocess
+// counted them. Emission is warp-cooperative: a lane writes the pairs of its own item when it has
+// at most 32 of them, and the whole warp writes the pairs of larger items (pole-stretched
+// Gaussians can cover hundreds of tiles), 32 consecutive columns at a time.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
@@ -16,7 +19,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t rect_tiles(uint2 r) { return (r.x >> 16) * (r.y >> 16); }
+__device__ __forceinline__ uint32_t rect_tiles(uint2 r) { return r.y; }
 
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* s) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -76,60 +79,99 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __rest
         unsigned long long used = total < capacity ? total : capacity;
         hdr->pairs_emitted = used;
         hdr->n_pairs_sort = (uint32_t)used;
+        hdr->n_big = 0u;
+        hdr->big_next = 0u;
         if (total > capacity) atomicOr(&hdr->status, kStCapacity);
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_emit(const uint32_t* __restrict__ sorted_idx,
-                                                      const uint2* __restrict__ rect,
-                                                      const ViewDev* __restrict__ views, int n_per_view,
-                                                      uint32_t n_items,
-                                                      const unsigned long long* __restrict__ block_offsets,
-                                                      unsigned long long capacity, uint32_t* __restrict__ keys,
-                                                      uint32_t* __restrict__ vals) {
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-    uint32_t idx[kScanItems];
-    uint2 rc[kScanItems];
-    unsigned long long cnt = 0ull;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        uint32_t k = base + j;
-        idx[j] = k < n_items ? sorted_idx[k] : 0u;
-        rc[j] = k < n_items ? rect[idx[j]] : make_uint2(0u, 0u);
-        cnt += rect_tiles(rc[j]);
-    }
-    // block exclusive scan of the per-thread counts
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long x = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    unsigned long long off = block_offsets[blockIdx.x] + x - cnt;
-    for (int k = 0; k < w; ++k) off += s_warp[k];
-#pragma unroll 1
-    for (int j = 0; j < kScanItems; ++j) {
-        const uint2 r = rc[j];
-        const uint32_t ntx = r.x >> 16, nty = r.y >> 16;
-        if (ntx == 0u || nty == 0u) continue;
-        const uint32_t tx0 = r.x & 0xFFFFu, ty0 = r.y & 0xFFFFu;
-        const int v = (int)(idx[j] / (uint32_t)n_per_view);
-        const ViewDev& V = views[v];
-        for (uint32_t ty = 0; ty < nty; ++ty) {
-            const uint32_t row = (uint32_t)V.tile_base + (ty0 + ty) * (uint32_t)V.tiles_x;
-            uint32_t tx = tx0;
-            for (uint32_t k = 0; k < ntx; ++k) {
-                if (off < capacity) {
-                    keys[off] = row + tx;
-                    vals[off] = idx[j];
-                }
-                ++off;
-                if (++tx == (uint32_t)V.tiles_x) tx = 0u;
-            }
+// Writes the pairs of one row band: columns start .. start + cnt - 1 (mod tiles_x), lanes
+// [lane0, lane0 + nlanes) sharing the work.
+__device__ __forceinline__ void write_band(uint32_t row, int start, int cnt, int tiles_x, uint32_t idx,
+                                           unsigned long long off, unsigned long long capacity, int lane0,
+                                           int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (int k = lane0; k < cnt; k += nlanes) {
+        const unsigned long long o = off + (unsigned long long)k;
+        if (o < capacity) {
+            int tx = start + k;
+            if (tx >= tiles_x) tx -= tiles_x;
+            keys[o] = row + (uint32_t)tx;
+            vals[o] = idx;
         }
+    }
+}
+
+// Emits all pairs of one item from offset off; lanes [lane0, lane0 + nlanes) cooperate.
+__device__ __forceinline__ void emit_item(uint32_t idx, unsigned long long off, const float4* __restrict__ rec_a,
+                                          const float4* __restrict__ rec_b, const ViewDev* __restrict__ views,
+                                          int n_per_view, int tw, int th, unsigned long long capacity, int lane0,
+                                          int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const ViewDev& V = views[idx / (uint32_t)n_per_view];
+    Footprint fp = make_footprint(rec_a[idx], rec_b[idx]);
+    int jlo, jhi;
+    footprint_rows(fp, V.H, jlo, jhi);
+    if (jlo > jhi) return;
+    for (int ty = jlo / th; ty <= jhi / th; ++ty) {
+        int start, cnt;
+        band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, tw, V.tiles_x, start, cnt);
+        const uint32_t row = (uint32_t)V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x;
+        write_band(row, start, cnt, V.tiles_x, idx, off, capacity, lane0, nlanes, keys, vals);
+        off += (unsigned long long)cnt;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t base = blockIdx.x * kScanTile;
+    if (tid == 0) s_carry = a.block_offsets[blockIdx.x];
+    __syncthreads();
+    for (int round = 0; round < kScanItems; ++round) {
+        const uint32_t k = base + (uint32_t)(round * kScanThreads + tid);
+        const uint32_t idx = k < a.n_items ? a.sorted_idx[k] : 0u;
+        const uint32_t cnt = k < a.n_items ? a.rect[idx].y : 0u;
+        // block-wide exclusive scan of the counts of this round (items in depth order)
+        unsigned long long x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[w] = x;
+        __syncthreads();
+        unsigned long long off = s_carry + x - cnt, tot = 0ull;
+        for (int j = 0; j < kScanThreads / 32; ++j) {
+            const unsigned long long v = s_warp[j];
+            if (j < w) off += v;
+            tot += v;
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += tot;
+        // small items: one lane each
+        if (cnt > 0u && cnt <= 32u)
+            emit_item(idx, off, a.rec_a, a.rec_b, a.views, a.n_per_view, a.tile_w, a.tile_h, a.capacity, 0, 1,
+                      a.keys, a.vals);
+        // large items: queued for k_emit_big (whole warps, dynamically scheduled). Depth order
+        // clusters the nearest, largest Gaussians into the first blocks, so serving them here
+        // would leave a few warps writing most of the pairs.
+        if (cnt > 32u) {
+            const uint32_t slot = atomicAdd(&a.hdr->n_big, 1u);
+            a.big[slot] = make_uint2(idx, (uint32_t)off);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_big = a.hdr->n_big;
+    for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(&a.hdr->big_next, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n_big) break;
+        const uint2 e = a.big[i];
+        emit_item(e.x, (unsigned long long)e.y, a.rec_a, a.rec_b, a.views, a.n_per_view, a.tile_w, a.tile_h,
+                  a.capacity, lane, 32, a.keys, a.vals);
     }
 }
 
@@ -158,10 +200,16 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
     if (nb > 0) {
-        k_emit<<<nb, kScanThreads, 0, st>>>(a.sorted_idx, a.rect, a.views, a.n_per_view, a.n_items, a.block_sums,
-                                            a.capacity, a.keys, a.vals);
+        EmitArgs ea{};
+        ea.sorted_idx = a.sorted_idx; ea.rect = a.rect; ea.rec_a = a.rec_a; ea.rec_b = a.rec_b; ea.views = a.views;
+        ea.n_per_view = a.n_per_view; ea.n_items = a.n_items; ea.tile_w = a.tile_w; ea.tile_h = a.tile_h;
+        ea.block_offsets = a.block_sums; ea.capacity = a.capacity; ea.keys = a.keys; ea.vals = a.vals;
+        ea.big = a.big; ea.hdr = a.hdr;
+        k_emit<<<nb, kScanThreads, 0, st>>>(ea);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        *launches += 1;
+        k_emit_big<<<a.num_sms * 4, 256, 0, st>>>(ea);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 2;
     }
     return cudaSuccess;
 }

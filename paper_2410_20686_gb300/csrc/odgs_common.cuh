@@ -53,7 +53,9 @@ struct Header {
     uint32_t n_pairs_sort;            // 32-bit copy of pairs_emitted for the sort kernels
     uint32_t work_fwd;
     uint32_t work_bwd;
-    uint32_t pad[1];
+    uint32_t n_big;                   // items queued for the warp-wide emission
+    uint32_t big_next;                // work counter of that emission
+    uint32_t pad[3];
 };
 
 struct Settings {
@@ -161,6 +163,84 @@ __device__ __forceinline__ void gather_records(const float4* __restrict__ ra, co
         b = make_float4(1.f, 0.f, 1.f, 0.f);
         c = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+}
+
+// ------------------------------------------------------------------ footprint on tiles
+// The set {alpha >= 1/255} of an item is the ellipse d^T conic d <= Q with Q = 2 ln(255 o);
+// binning uses an inflated Qb (stored in rec_b.w). For each tile row the ellipse's slice over the
+// row band's pixel-centre rows is one interval of columns, so the tiles an item is listed in are
+// exactly the tiles of each row band that meet that interval (seam-wrapped). The preprocess
+// counts them and the emission writes them with these same functions on the same stored floats,
+// in round-to-nearest intrinsics only, so both agree bit for bit.
+struct Footprint {
+    int c0, r0;
+    float du, dv;
+    float A, B, C;   // Sigma_2D recovered from the stored conic
+    float BC;        // B / C: centre line of the horizontal slices
+    float k;         // sqrt(det / C): half-width scale of the slices
+    float Qb;
+    float ev;        // vertical half extent sqrt(Qb C)
+    float ystar;     // dy of the rightmost point, B sqrt(Qb / A)
+};
+
+__device__ __forceinline__ Footprint make_footprint(float4 ra, float4 rb) {
+    Footprint f;
+    uint32_t packed = __float_as_uint(ra.z);
+    f.c0 = (int)(packed & 0xFFFFu);
+    f.r0 = (int)(packed >> 16);
+    f.du = ra.x;
+    f.dv = ra.y;
+    const float det = __fsub_rn(__fmul_rn(rb.x, rb.z), __fmul_rn(rb.y, rb.y));
+    f.A = __fdiv_rn(rb.z, det);
+    f.B = __fdiv_rn(-rb.y, det);
+    f.C = __fdiv_rn(rb.x, det);
+    f.Qb = rb.w;
+    f.BC = __fdiv_rn(f.B, f.C);
+    f.k = __fsqrt_rn(fmaxf(__fsub_rn(f.A, __fmul_rn(f.BC, f.B)), 0.f));
+    f.ev = __fsqrt_rn(__fmul_rn(f.Qb, f.C));
+    f.ystar = __fmul_rn(f.B, __fsqrt_rn(__fdiv_rn(f.Qb, f.A)));
+    return f;
+}
+
+__device__ __forceinline__ int floor_div_i(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Pixel rows [jlo, jhi] the footprint can reach (clipped to the image); empty if jlo > jhi.
+__device__ __forceinline__ void footprint_rows(const Footprint& f, int H, int& jlo, int& jhi) {
+    const float ev = fminf(f.ev, 2.f * (float)H);
+    jlo = max(0, f.r0 + (int)ceilf(__fsub_rn(f.dv, ev)));
+    jhi = min(H - 1, f.r0 + (int)floorf(__fadd_rn(f.dv, ev)));
+}
+
+// Horizontal offset of the slice boundary at vertical offset y (side = +1 right, -1 left).
+__device__ __forceinline__ float slice_edge(const Footprint& f, float y, float side) {
+    const float q = fmaxf(__fsub_rn(f.Qb, __fdiv_rn(__fmul_rn(y, y), f.C)), 0.f);
+    return __fadd_rn(__fmul_rn(f.BC, y), side * __fmul_rn(f.k, __fsqrt_rn(q)));
+}
+
+// Tile columns of the band of pixel rows [J0, J1]: start column (mod tiles_x) and count (0 if
+// the slice holds no pixel centre).
+__device__ __forceinline__ void band_columns(const Footprint& f, int J0, int J1, int W, int tw, int tiles_x,
+                                             int& start, int& count) {
+    const float d0 = fmaxf(__fsub_rn((float)(J0 - f.r0), f.dv), -f.ev);
+    const float d1 = fminf(__fsub_rn((float)(J1 - f.r0), f.dv), f.ev);
+    count = 0;
+    start = 0;
+    if (!(d0 <= d1)) return;
+    const float yr = fminf(fmaxf(f.ystar, d0), d1);
+    const float yl = fminf(fmaxf(-f.ystar, d0), d1);
+    const float xmax = __fadd_rn(slice_edge(f, yr, 1.f), 0.01f);
+    const float xmin = __fsub_rn(slice_edge(f, yl, -1.f), 0.01f);
+    const float half = (float)W;
+    if (!(xmax - xmin < half)) { start = 0; count = tiles_x; return; }
+    const int ilo = f.c0 + (int)ceilf(__fadd_rn(f.du, xmin));
+    const int ihi = f.c0 + (int)floorf(__fadd_rn(f.du, xmax));
+    if (ihi < ilo) return;
+    if (ihi - ilo + 1 >= W) { start = 0; count = tiles_x; return; }
+    const int tlo = floor_div_i(ilo, tw), thi = floor_div_i(ihi, tw);
+    const int n = thi - tlo + 1;
+    if (n >= tiles_x) { start = 0; count = tiles_x; return; }
+    start = ((tlo % tiles_x) + tiles_x) % tiles_x;
+    count = n;
 }
 
 // Offset from the Gaussian centre to the pixel centre (fi, fj are the integer pixel indices).

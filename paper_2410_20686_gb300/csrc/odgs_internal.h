@@ -40,6 +40,8 @@ struct PreBwdArgs {
 struct BinArgs {
     const uint32_t* sorted_idx;
     const uint2* rect;
+    const float4 *rec_a, *rec_b;
+    int tile_w, tile_h;
     const ViewDev* views;
     int n_per_view;
     uint32_t n_items;
@@ -47,6 +49,23 @@ struct BinArgs {
     Header* hdr;
     unsigned long long capacity;
     uint32_t *keys, *vals;
+    uint2* big;  // [n_items] queue of (item, offset) with more than 32 pairs
+    int num_sms;
+};
+
+struct EmitArgs {
+    const uint32_t* sorted_idx;
+    const uint2* rect;
+    const float4 *rec_a, *rec_b;
+    const ViewDev* views;
+    int n_per_view;
+    uint32_t n_items;
+    int tile_w, tile_h;
+    const unsigned long long* block_offsets;
+    unsigned long long capacity;
+    uint32_t *keys, *vals;
+    uint2* big;
+    Header* hdr;
 };
 
 struct FwdArgs {

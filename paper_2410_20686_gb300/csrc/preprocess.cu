@@ -278,30 +278,26 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
                 ok = c2.det > 0.f;
                 if (ok) {
                     float inv = 1.f / c2.det;
-                    float ca = c2.C * inv, cb = -c2.B * inv, cc = c2.A * inv;
-                    // conservative pixel rectangle of {alpha >= 1/255}; seam wrap in u
-                    float eu = sqrtf(Qb * c2.A), ev = sqrtf(Qb * c2.C);
-                    uint32_t tx0, ntx;
-                    const int tw = a.st.tile_w, th = a.st.tile_h;
-                    bool allcols = eu >= (float)V.W;
-                    if (!allcols) {
-                        int ilo = c0 + (int)ceilf(du - eu), ihi = c0 + (int)floorf(du + eu);
-                        if (ihi < ilo) ok = false;
-                        allcols = ihi - ilo + 1 >= V.W;
-                        int tlo = floor_div(ilo, tw), thi = floor_div(ihi, tw);
-                        int n = thi - tlo + 1;
-                        if (n >= V.tiles_x) allcols = true;
-                        ntx = (uint32_t)n;
-                        tx0 = (uint32_t)(((tlo % V.tiles_x) + V.tiles_x) % V.tiles_x);
+                    const float4 ra = make_float4(du, dv, __uint_as_float((uint32_t)c0 | ((uint32_t)r0 << 16)), o);
+                    const float4 rb = make_float4(c2.C * inv, -c2.B * inv, c2.A * inv, Qb);
+                    // tiles met by the footprint, row band by row band (seam-wrapped columns)
+                    Footprint fp = make_footprint(ra, rb);
+                    int jlo, jhi;
+                    footprint_rows(fp, V.H, jlo, jhi);
+                    uint32_t count = 0u;
+                    const int th = a.st.tile_h;
+                    const int ty0 = jlo / th, ty1 = jhi / th;
+                    if (jlo <= jhi) {
+                        for (int ty = ty0; ty <= ty1; ++ty) {
+                            int st0, cnt;
+                            band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.st.tile_w,
+                                         V.tiles_x, st0, cnt);
+                            count += (uint32_t)cnt;
+                        }
                     }
-                    if (allcols) { tx0 = 0u; ntx = (uint32_t)V.tiles_x; }
-                    ev = fminf(ev, 2.f * V.H);
-                    int jlo = max(0, r0 + (int)ceilf(dv - ev)), jhi = min(V.H - 1, r0 + (int)floorf(dv + ev));
-                    if (jhi < jlo) ok = false;
-                    if (ok) {
-                        uint32_t ty0 = (uint32_t)(jlo / th), nty = (uint32_t)(jhi / th) - ty0 + 1u;
-                        rect = make_uint2(tx0 | (ntx << 16), ty0 | (nty << 16));
-                        local_pairs += (unsigned long long)ntx * nty;
+                    if (count > 0u) {
+                        rect = make_uint2((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count);
+                        local_pairs += count;
                         key = __float_as_uint(r);
                         // view-dependent colour: max(0, sum_k sh_k Y_k(d) + 0.5), d from the
                         // camera centre to the mean in world space
@@ -317,8 +313,8 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
                             for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
                             rgb[ch] = fmaxf(acc, 0.f);
                         }
-                        a.rec_a[item] = make_float4(du, dv, __uint_as_float((uint32_t)c0 | ((uint32_t)r0 << 16)), o);
-                        a.rec_b[item] = make_float4(ca, cb, cc, 0.f);
+                        a.rec_a[item] = ra;
+                        a.rec_b[item] = rb;
                         a.rec_c[item] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
                     }
                 }

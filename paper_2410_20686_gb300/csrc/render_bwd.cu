@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
         }
         __syncthreads();
         const int maxn = s_maxn;
+        const int wmax = __reduce_max_sync(0xffffffffu, (unsigned)nl);  // warp-uniform bound
         evals += (uint32_t)nl;
 
         for (int hi = maxn; hi > 0; hi -= B) {
@@ -132,6 +133,11 @@ __global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
             const int any_split = __syncthreads_or(split);
             for (int j = cnt - 1; j >= 0; --j) {
                 const int e = lo + j;
+                float* red = s_red + ((size_t)j * nwarps + warp) * 9;
+                if (e >= wmax) {  // no pixel of this warp reached entry e in the forward pass
+                    if (lane < 9) red[lane] = 0.f;
+                    continue;
+                }
                 float vals[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) vals[k] = 0.f;
@@ -169,14 +175,19 @@ __global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
                         }
                     }
                 }
-                float* red = s_red + ((size_t)j * nwarps + warp) * 9;
-                if (__any_sync(0xffffffffu, contrib)) {
+                const unsigned m = __ballot_sync(0xffffffffu, contrib);
+                if (m == 0u) {
+                    if (lane < 9) red[lane] = 0.f;
+                } else if ((m & (m - 1u)) == 0u) {  // one contributing pixel: no reduction needed
+                    if (contrib) {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) red[k] = vals[k];
+                    }
+                } else {
                     int vi;
                     bool ok;
-                    const float s = warp_reduce9(vals, lane, &vi, &ok);
-                    if (ok) red[vi] = s;
-                } else if (lane < 9) {
-                    red[lane] = 0.f;
+                    const float sm = warp_reduce9(vals, lane, &vi, &ok);
+                    if (ok) red[vi] = sm;
                 }
             }
             __syncthreads();

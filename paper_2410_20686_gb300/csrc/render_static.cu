@@ -134,6 +134,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     uint32_t* d_lb = reinterpret_cast<uint32_t*>(take(4 * radix_lookback_words(n)));
     uint32_t* p_hist = reinterpret_cast<uint32_t*>(take(4 * 4 * 256));
     uint32_t* p_ctr = reinterpret_cast<uint32_t*>(take(4 * 4));
+    uint2* big = reinterpret_cast<uint2*>(take(sizeof(uint2) * n));
     if (o >= kStaticBytes) return ODGS_ERR_WORKSPACE;
     // the rest holds the pairs: two key and two value buffers plus the sort look-back words
     const size_t rem = kStaticBytes - o;
@@ -165,8 +166,10 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
         return ODGS_ERR_CUDA;
     BinArgs b{};
     b.sorted_idx = dv[rb]; b.rect = rect; b.views = vd; b.n_per_view = g->n > 0 ? g->n : 1;
+    b.rec_a = rec_a; b.rec_b = rec_b; b.tile_w = st.tile_w; b.tile_h = st.tile_h;
     b.n_items = (uint32_t)n; b.block_sums = block_sums; b.hdr = hdr; b.capacity = cap;
     b.keys = pk[0]; b.vals = pv[0];
+    b.big = big; b.num_sms = num_sms;
     if (launch_binning(b, strm, &launches) != cudaSuccess) return ODGS_ERR_CUDA;
     int rp = 0;
     if (launch_radix_sort(pk, pv, &hdr->n_pairs_sort, cap, key_bits, p_hist, p_ctr, p_lb, &hdr->status, num_sms,
