@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--width", type=int, default=2048)
     ap.add_argument("--tile", type=str, default="16x16")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the blend kernels (0 = auto)")
     return ap.parse_args()
 
 
@@ -230,7 +231,7 @@ def run_ours(args):
             dist.barrier()
 
     tw, th = (int(x) for x in args.tile.split("x"))
-    rs = RenderSettings(sh_degree=3, tile_w=tw, tile_h=th, batch=args.batch)
+    rs = RenderSettings(sh_degree=3, tile_w=tw, tile_h=th, batch=args.batch, pixels_per_thread=args.ppt)
     scene = S.config2(n=args.n, width=args.width)
     target_np = S.target_images(scene, 2)[0]
     view = scene.views[0]
@@ -354,7 +355,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2,
-                      "sh_degree": 3, "tile": args.tile, "batch": args.batch,
+                      "sh_degree": 3, "tile": args.tile, "batch": args.batch, "pixels_per_thread": args.ppt,
                       "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
                       "parallelism": f"replicas x{world}"},
            "roofline": roofline, "kernels_ms": kern, "gpu_launches": launches_per_step * K, "clocks": clocks}

@@ -75,6 +75,9 @@ typedef struct {
     float bg[3];        /* background colour blended with the final transmittance        */
     int recompute_lists;/* 1: odgs_render_bwd re-runs preprocess + bin_sort itself        */
     int grad_accumulate;/* 1: gradients are added (+=) to the output arrays; 0: written  */
+    int pixels_per_thread; /* blend kernels: pixels of one row per thread, 1, 2 or 4;
+                              0 -> the largest that divides tile_w while tile_w * tile_h /
+                              pixels_per_thread is a multiple of 32 and at most 256         */
 } odgs_settings;
 
 /* Gaussian parameters, device pointers, float32, contiguous:

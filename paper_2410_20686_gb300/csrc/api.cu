@@ -93,6 +93,8 @@ odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
     if (!(t.tile_w == 8 || t.tile_w == 16 || t.tile_w == 32)) return ODGS_ERR_INVALID_ARG;
     const int area = t.tile_w * t.tile_h;
     if (t.tile_h < 1 || area < 32 || area > 1024 || area % 32 != 0) return ODGS_ERR_INVALID_ARG;
+    t.pixels_per_thread = pixels_per_thread(t.tile_w, t.tile_h, t.pixels_per_thread);
+    if (t.pixels_per_thread == 0) return ODGS_ERR_INVALID_ARG;
     if (t.batch == 0) t.batch = 64;
     if (t.batch < 1 || t.batch > 256) return ODGS_ERR_INVALID_ARG;
     if (!finite(t.cov_dilation) || t.cov_dilation < 0.f) return ODGS_ERR_INVALID_ARG;
@@ -282,7 +284,8 @@ odgs_status odgs_preprocess(odgs_ctx* c, const odgs_gaussians* g, const odgs_vie
     c->stage = 0;
     c->launches = 0;
     c->bwd_batch = std::min(st.batch, 64);
-    while (c->bwd_batch > 8 && render_bwd_smem(c->bwd_batch, st.tile_w * st.tile_h) > 48 * 1024) c->bwd_batch /= 2;
+    const int bwd_threads = st.tile_w * st.tile_h / st.pixels_per_thread;
+    while (c->bwd_batch > 8 && render_bwd_smem(c->bwd_batch, bwd_threads) > 48 * 1024) c->bwd_batch /= 2;
     r = run_preprocess(c, static_cast<cudaStream_t>(stream));
     if (r != ODGS_OK) return r;
     c->stage = 1;
@@ -395,6 +398,7 @@ odgs_status odgs_render_fwd(odgs_ctx* c, float* const* images, float* const* fin
     a.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
     a.n_views = c->V; a.total_tiles = c->geo.total_tiles;
     a.tile_w = c->s.tile_w; a.tile_h = c->s.tile_h; a.batch = c->s.batch;
+    a.ppt = c->s.pixels_per_thread;
     a.n_items = (uint32_t)c->geo.n_items;
     a.ranges = reinterpret_cast<const uint2*>(w + c->L.ranges);
     a.pair_vals = c->sorted_vals;
@@ -412,8 +416,7 @@ odgs_status odgs_render_fwd(odgs_ctx* c, float* const* images, float* const* fin
     if (cudaMemsetAsync(&hdr->work_fwd, 0, sizeof(uint32_t), st) != cudaSuccess) return ODGS_ERR_CUDA;
     if (cudaMemsetAsync(&hdr->evals_fwd, 0, sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
     if (cudaMemsetAsync(&hdr->blended, 0, sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
-    const int threads = c->s.tile_w * c->s.tile_h;
-    const int grid = persistent_grid(c, render_fwd_occupancy(threads, a.batch));
+    const int grid = persistent_grid(c, render_fwd_occupancy(c->s.tile_w, c->s.tile_h, a.batch, a.ppt));
     if (launch_render_fwd(a, grid, st) != cudaSuccess) return ODGS_ERR_CUDA;
     c->launches += 1;
     c->stage = 3;
@@ -443,6 +446,7 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
     a.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
     a.n_views = c->V; a.total_tiles = c->geo.total_tiles;
     a.tile_w = c->s.tile_w; a.tile_h = c->s.tile_h; a.batch = c->bwd_batch;
+    a.ppt = c->s.pixels_per_thread;
     a.n_items = (uint32_t)c->geo.n_items;
     a.ranges = reinterpret_cast<const uint2*>(w + c->L.ranges);
     a.pair_vals = c->sorted_vals;
@@ -455,8 +459,7 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
     for (int i = 0; i < 3; ++i) a.bg[i] = c->s.bg[i];
     a.acc = acc;
     a.hdr = hdr;
-    const int threads = c->s.tile_w * c->s.tile_h;
-    const int grid = persistent_grid(c, render_bwd_occupancy(threads, a.batch));
+    const int grid = persistent_grid(c, render_bwd_occupancy(c->s.tile_w, c->s.tile_h, a.batch, a.ppt));
     if (launch_render_bwd(a, grid, st) != cudaSuccess) return ODGS_ERR_CUDA;
     c->launches += 1;
     c->stage = 4;

@@ -70,7 +70,7 @@ struct EmitArgs {
 
 struct FwdArgs {
     const ViewDev* views;
-    int n_views, total_tiles, tile_w, tile_h, batch;
+    int n_views, total_tiles, tile_w, tile_h, batch, ppt;
     uint32_t n_items;
     const uint2* ranges;
     const uint32_t* pair_vals;
@@ -85,7 +85,7 @@ struct FwdArgs {
 
 struct BwdArgs {
     const ViewDev* views;
-    int n_views, total_tiles, tile_w, tile_h, batch;
+    int n_views, total_tiles, tile_w, tile_h, batch, ppt;
     uint32_t n_items;
     const uint2* ranges;
     const uint32_t* pair_vals;
@@ -116,8 +116,11 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const Header* hdr, uint2* r
 
 size_t render_fwd_smem(int batch);
 size_t render_bwd_smem(int batch, int threads);
-int render_fwd_occupancy(int threads, int batch);
-int render_bwd_occupancy(int threads, int batch);
+// Pixels per thread of the blend kernels for a tile shape: `want` (1, 2, 4) if it fits, the
+// largest that fits when want == 0, and 0 when the shape (or the wish) is not supported.
+int pixels_per_thread(int tile_w, int tile_h, int want = 0);
+int render_fwd_occupancy(int tile_w, int tile_h, int batch, int ppt);
+int render_bwd_occupancy(int tile_w, int tile_h, int batch, int ppt);
 cudaError_t launch_render_fwd(const FwdArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_render_bwd(const BwdArgs& a, int grid, cudaStream_t st);
 

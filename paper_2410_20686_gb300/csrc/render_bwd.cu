@@ -1,16 +1,20 @@
 // Backward alpha blending (reverse of Eq. 3) on ERP tiles (sm_103a).
 //
-// Same persistent (view, tile) schedule as the forward kernel. Each pixel starts from its final
-// transmittance and the index after its last blended Gaussian, and walks its tile list back to
-// front, recovering T_j = T_{j+1} / (1 - alpha_j). Per blended Gaussian it forms
+// Same persistent (view, tile) schedule and PPT-pixels-per-thread layout as the forward kernel.
+// Each pixel starts from its final transmittance and the index after its last blended Gaussian,
+// and walks its tile list back to front, recovering T_j = T_{j+1} / (1 - alpha_j). Per blended
+// Gaussian it forms
 //   dL/drgb = alpha T g,   dL/dalpha = T (rgb . g) - (B . g) / (1 - alpha),
 // with g = dL/dC and B the colour blended behind the Gaussian (background included), and from
 // dL/dalpha the gradients w.r.t. opacity, conic (a, b, c) and ERP mean (u, v) through Eq. 2
-// (zero when alpha was clamped at 0.99).
+// (zero when alpha was clamped at 0.99). The skip / clamp decisions and alpha are recomputed
+// with the forward kernel's exact operation sequence, so they match it bit for bit.
 //
-// The nine per-Gaussian values are summed over the 32 pixels of a warp with a transpose
-// reduction (12 shuffles instead of 45), over the warps of the CTA in shared memory, and then
-// added to the per-(view, Gaussian) accumulator with three 16-byte vector atomics.
+// A thread first sums the nine values over its PPT pixels; the warp then sums them over its
+// lanes with a transpose reduction (12 shuffles for 9 values), the CTA over its warps in shared
+// memory, and the result is added to the per-(view, Gaussian) accumulator with three 16-byte
+// vector atomics. A warp whose pixels all stopped before an entry skips it; a warp with a single
+// contributing lane skips the reduction.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
@@ -56,8 +60,8 @@ __device__ __forceinline__ float warp_reduce9(const float v[9], int lane, int* v
     return z;
 }
 
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
+template <int PPT>
+__global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
     extern __shared__ float4 smem[];
     const int B = a.batch;
     const int nwarps = blockDim.x >> 5;
@@ -73,7 +77,8 @@ __global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int tw = a.tile_w;
-    const int lx = tid % tw, ly = tid / tw;
+    const int tpr = tw / PPT;
+    const int lx0 = (tid % tpr) * PPT, ly = tid / tpr;
     uint32_t evals = 0u;
 
     for (;;) {
@@ -91,27 +96,33 @@ __global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
         const int lt = item - V.tile_base;
         const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
         const int x0 = tx * tw;
-        const int x = x0 + lx, y = ty * a.tile_h + ly;
+        const int xp = x0 + lx0, y = ty * a.tile_h + ly;
         const bool inside = y < V.H;
-        const float fi = (float)x, fj = (float)y;
+        const float fi0 = (float)xp, fj = (float)y;
         const uint2 rg = a.ranges[item];
 
-        float T = 1.f, Bg = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        int nl = 0;
-        if (inside) {
-            const int pix = y * V.W + x;
-            const int HW = V.W * V.H;
-            T = a.T_final[V.pix_base + pix];
-            nl = (int)a.n_last[V.pix_base + pix];
-            const float* gi = a.dL_dimages[v];
-            g0 = gi[pix]; g1 = gi[HW + pix]; g2 = gi[2 * HW + pix];
-            Bg = T * (a.bg[0] * g0 + a.bg[1] * g1 + a.bg[2] * g2);
-            if (nl > 0) atomicMax(&s_maxn, nl);
+        float T[PPT], Bg[PPT], g0[PPT], g1[PPT], g2[PPT];
+        int nl[PPT];
+        int tmax = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            T[k] = 1.f; Bg[k] = 0.f; g0[k] = g1[k] = g2[k] = 0.f; nl[k] = 0;
+            if (inside) {
+                const int pix = y * V.W + xp + k;
+                const int HW = V.W * V.H;
+                T[k] = a.T_final[V.pix_base + pix];
+                nl[k] = (int)a.n_last[V.pix_base + pix];
+                const float* gi = a.dL_dimages[v];
+                g0[k] = gi[pix]; g1[k] = gi[HW + pix]; g2[k] = gi[2 * HW + pix];
+                Bg[k] = T[k] * (a.bg[0] * g0[k] + a.bg[1] * g1[k] + a.bg[2] * g2[k]);
+                tmax = max(tmax, nl[k]);
+                evals += (uint32_t)nl[k];
+            }
         }
+        if (tmax > 0) atomicMax(&s_maxn, tmax);
         __syncthreads();
         const int maxn = s_maxn;
-        const int wmax = __reduce_max_sync(0xffffffffu, (unsigned)nl);  // warp-uniform bound
-        evals += (uint32_t)nl;
+        const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)tmax);  // warp-uniform bound
 
         for (int hi = maxn; hi > 0; hi -= B) {
             const int lo = max(0, hi - B);
@@ -140,48 +151,73 @@ __global__ void __launch_bounds__(MAXT) k_render_bwd(BwdArgs a) {
                 }
                 float vals[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) vals[k] = 0.f;
+                for (int q = 0; q < 9; ++q) vals[q] = 0.f;
                 bool contrib = false;
-                if (e < nl) {
+                if (e < tmax) {
                     const float4 P = s_pos[j];
-                    const float4 c = s_col[j];
-                    const float fc = (any_split && fi >= c.w) ? s_fc2[j] : P.x;
-                    float dx, dy;
-                    pixel_offset(fi, fj, fc, P, dx, dy);
-                    const float p = gauss_exponent(s_con[j], dx, dy);
-                    if (p >= kLog2AlphaMin) {
+                    const float4 K = s_con[j];
+                    const float dy = __fsub_rn(__fsub_rn(fj, P.y), P.w);
+                    const float Bdy = __fmul_rn(K.y, dy);
+                    const float rr = __fmaf_rn(__fmul_rn(K.z, dy), dy, K.w);
+                    // exponents of all PPT pixels first (the forward kernel's exact sequence)
+                    float pk[PPT], dxk[PPT];
+                    if (!any_split) {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            dxk[k] = __fsub_rn(__fsub_rn(fi0 + (float)k, P.x), P.z);
+                            pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
+                        }
+                    } else {
+                        const float fsplit = s_col[j].w, fc2 = s_fc2[j];
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            const float fi = fi0 + (float)k;
+                            dxk[k] = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), P.z);
+                            pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
+                        }
+                    }
+                    bool any = false;
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) any |= (e < nl[k]) & (pk[k] >= kLog2AlphaMin);
+                    if (any) {
                         contrib = true;
-                        const float ar = exp2f(p);
-                        const float alpha = fminf(kAlphaMax, ar);
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float Tj = __fdiv_rn(T, om);
-                        const float w = alpha * Tj;
-                        const float cg = c.x * g0 + c.y * g1 + c.z * g2;
-                        vals[6] = w * g0;
-                        vals[7] = w * g1;
-                        vals[8] = w * g2;
-                        const float dLda = Tj * cg - Bg / om;
-                        Bg = fmaf(cg, w, Bg);
-                        T = Tj;
-                        if (ar < kAlphaMax) {
-                            const float4 R = s_raw[j];
-                            const float dp = dLda * alpha;  // dL/d(power), power = ln G
-                            vals[5] = dp * R.w;
-                            vals[2] = dp * (-0.5f * dx * dx);
-                            vals[3] = dp * (-dx * dy);
-                            vals[4] = dp * (-0.5f * dy * dy);
-                            vals[0] = dp * (R.x * dx + R.y * dy);
-                            vals[1] = dp * (R.y * dx + R.z * dy);
+                        const float4 c = s_col[j];
+                        const float4 R = s_raw[j];
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
+                            const float dx = dxk[k];
+                            const float ar = exp2f(pk[k]);
+                            const float alpha = fminf(kAlphaMax, ar);
+                            const float inv = __fdividef(1.f, __fsub_rn(1.f, alpha));
+                            const float Tj = T[k] * inv;
+                            const float w = alpha * Tj;
+                            const float cg = c.x * g0[k] + c.y * g1[k] + c.z * g2[k];
+                            vals[6] += w * g0[k];
+                            vals[7] += w * g1[k];
+                            vals[8] += w * g2[k];
+                            const float dLda = Tj * cg - Bg[k] * inv;
+                            Bg[k] = fmaf(cg, w, Bg[k]);
+                            T[k] = Tj;
+                            if (ar < kAlphaMax) {
+                                const float dp = dLda * alpha;  // dL/d(power), power = ln G
+                                vals[5] += dp * R.w;
+                                vals[2] += dp * (-0.5f * dx * dx);
+                                vals[3] += dp * (-dx * dy);
+                                vals[4] += dp * (-0.5f * dy * dy);
+                                vals[0] += dp * (R.x * dx + R.y * dy);
+                                vals[1] += dp * (R.y * dx + R.z * dy);
+                            }
                         }
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, contrib);
                 if (m == 0u) {
                     if (lane < 9) red[lane] = 0.f;
-                } else if ((m & (m - 1u)) == 0u) {  // one contributing pixel: no reduction needed
+                } else if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction needed
                     if (contrib) {
 #pragma unroll
-                        for (int k = 0; k < 9; ++k) red[k] = vals[k];
+                        for (int q = 0; q < 9; ++q) red[q] = vals[q];
                     }
                 } else {
                     int vi;
@@ -215,37 +251,31 @@ size_t render_bwd_smem(int batch, int threads) {
            (size_t)batch * (threads / 32) * 9 * sizeof(float);
 }
 
-int render_bwd_occupancy(int threads, int batch) {
+int render_bwd_occupancy(int tile_w, int tile_h, int batch, int ppt) {
+    if (ppt == 0) return 1;
+    const int threads = tile_w * tile_h / ppt;
+    const size_t sm = render_bwd_smem(batch, threads);
     int nb = 0;
-    size_t sm = render_bwd_smem(batch, threads);
     cudaError_t e;
-    if (threads <= 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<64>, threads, sm);
-    else if (threads <= 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<128>, threads, sm);
-    else if (threads <= 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<256>, threads, sm);
-    else if (threads <= 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<512>, threads, sm);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<1024>, threads, sm);
-    return e == cudaSuccess ? max(nb, 1) : 1;
-}
-
-template <int MAXT>
-static cudaError_t launch_bwd_t(const BwdArgs& a, int grid, cudaStream_t st) {
-    const int threads = a.tile_w * a.tile_h;
-    size_t sm = render_bwd_smem(a.batch, threads);
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_render_bwd<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+    switch (ppt) {
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<4>, threads, sm); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<2>, threads, sm); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<1>, threads, sm); break;
     }
-    k_render_bwd<MAXT><<<grid, threads, sm, st>>>(a);
-    return cudaGetLastError();
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 cudaError_t launch_render_bwd(const BwdArgs& a, int grid, cudaStream_t st) {
-    const int threads = a.tile_w * a.tile_h;
-    if (threads <= 64) return launch_bwd_t<64>(a, grid, st);
-    if (threads <= 128) return launch_bwd_t<128>(a, grid, st);
-    if (threads <= 256) return launch_bwd_t<256>(a, grid, st);
-    if (threads <= 512) return launch_bwd_t<512>(a, grid, st);
-    return launch_bwd_t<1024>(a, grid, st);
+    const int ppt = a.ppt;
+    if (ppt != 1 && ppt != 2 && ppt != 4) return cudaErrorInvalidValue;
+    const int threads = a.tile_w * a.tile_h / ppt;
+    const size_t sm = render_bwd_smem(a.batch, threads);
+    switch (ppt) {
+        case 4: k_render_bwd<4><<<grid, threads, sm, st>>>(a); break;
+        case 2: k_render_bwd<2><<<grid, threads, sm, st>>>(a); break;
+        default: k_render_bwd<1><<<grid, threads, sm, st>>>(a); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace odgs

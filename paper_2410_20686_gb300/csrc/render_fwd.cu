@@ -1,23 +1,28 @@
 // Forward alpha blending (Sec. 3.1, Eq. 2-3) on ERP tiles (sm_103a).
 //
 // A persistent grid pulls (view, tile) work items from an atomic counter, so one launch renders
-// any number of views of mixed resolution. For each tile the CTA (one thread per pixel) walks
-// the tile's depth-ordered list in batches: the threads gather a batch of records with 16-byte
-// loads, convert them to the tile's staged form (seam shift, base-2 conic, log2 opacity) in
-// shared memory, then every pixel evaluates the batch from shared memory (broadcast reads).
-// A pixel stops before the Gaussian that would take its transmittance below 1e-4; the tile
-// stops when all its pixels have stopped (__syncthreads_count).
+// any number of views of mixed resolution. For each tile the CTA walks the tile's depth-ordered
+// list in batches: the threads gather a batch of records with 16-byte loads, convert them to the
+// tile's staged form (seam shift, base-2 conic, log2 opacity) in shared memory, then evaluate the
+// batch from shared memory (broadcast reads).
+//
+// Each thread owns PPT consecutive pixels of one row. The row-constant part of Eq. 2's quadratic
+// form (B dy and C dy^2 + log2 o) and the shared-memory loads are paid once per thread and entry,
+// not once per pixel; the kernel is bound by instruction issue, so this is where its time goes.
+// A pixel stops before the Gaussian that would take its transmittance below 1e-4; a thread stops
+// when its pixels have; the tile stops when all threads have (__syncthreads_count).
 //
 // Per pixel the result depends only on the pixel, the Gaussians' records and their global
-// order, never on the tile shape or batch size: the offset to a Gaussian is formed from integer
-// pixel indices, and list entries with alpha < 1/255 leave the state untouched.
+// order, never on the tile shape, the batch size or PPT: the offset to a Gaussian is formed from
+// integer pixel indices, every pixel evaluates the same fixed sequence of round-to-nearest
+// operations, and list entries with alpha < 1/255 leave the state untouched.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
 namespace odgs {
 
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT) k_render_fwd(FwdArgs a) {
+template <int PPT>
+__global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
     extern __shared__ float4 smem[];
     const int B = a.batch;
     float4* s_pos = smem;
@@ -28,7 +33,8 @@ __global__ void __launch_bounds__(MAXT) k_render_fwd(FwdArgs a) {
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int tw = a.tile_w;
-    const int lx = tid % tw, ly = tid / tw;
+    const int tpr = tw / PPT;  // threads per pixel row
+    const int lx0 = (tid % tpr) * PPT, ly = tid / tpr;
     uint32_t evals = 0u, blended = 0u;  // (pixel, entry) evaluations / blends by this thread
 
     for (;;) {
@@ -43,15 +49,21 @@ __global__ void __launch_bounds__(MAXT) k_render_fwd(FwdArgs a) {
         const int lt = item - V.tile_base;
         const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
         const int x0 = tx * tw;
-        const int x = x0 + lx, y = ty * a.tile_h + ly;
+        const int xp = x0 + lx0, y = ty * a.tile_h + ly;
         const bool inside = y < V.H;
-        const float fi = (float)x, fj = (float)y;
+        const float fi0 = (float)xp, fj = (float)y;
         const uint2 rg = a.ranges[item];
         const int n = (int)(rg.y - rg.x);
 
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        int last = 0, tested = inside ? n : 0;
-        bool done = !inside;
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+        int last[PPT], tested[PPT];
+        bool done[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f;
+            last[k] = 0; tested[k] = inside ? n : 0; done[k] = !inside;
+        }
+        int alive = inside ? PPT : 0;
         for (int b0 = 0; b0 < n; b0 += B) {
             const int cnt = min(B, n - b0);
             int split = 0;
@@ -67,62 +79,71 @@ __global__ void __launch_bounds__(MAXT) k_render_fwd(FwdArgs a) {
                 split |= (s.col.w <= 1e30f);
             }
             const int any_split = __syncthreads_or(split);
-            if (!done) {
+            for (int j = 0; j < cnt && alive > 0; ++j) {
+                const float4 P = s_pos[j];
+                const float4 K = s_con[j];
+                const float dy = __fsub_rn(__fsub_rn(fj, P.y), P.w);
+                const float Bdy = __fmul_rn(K.y, dy);
+                const float rr = __fmaf_rn(__fmul_rn(K.z, dy), dy, K.w);
+                // exponents of all PPT pixels first: independent chains, no branches
+                float pk[PPT];
                 if (!any_split) {
-                    for (int j = 0; j < cnt; ++j) {
-                        const float4 P = s_pos[j];
-                        float dx, dy;
-                        pixel_offset(fi, fj, P.x, P, dx, dy);
-                        const float p = gauss_exponent(s_con[j], dx, dy);
-                        if (p < kLog2AlphaMin) continue;
-                        const float alpha = fminf(kAlphaMax, exp2f(p));
-                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                        if (Tn < kTMin) { done = true; tested = b0 + j + 1; break; }
-                        const float w = __fmul_rn(alpha, T);
-                        const float4 c = s_col[j];
-                        C0 = __fmaf_rn(c.x, w, C0);
-                        C1 = __fmaf_rn(c.y, w, C1);
-                        C2 = __fmaf_rn(c.z, w, C2);
-                        T = Tn;
-                        last = b0 + j + 1;
-                        ++blended;
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const float dx = __fsub_rn(__fsub_rn(fi0 + (float)k, P.x), P.z);
+                        pk[k] = __fmaf_rn(__fmaf_rn(K.x, dx, Bdy), dx, rr);
                     }
                 } else {
-                    for (int j = 0; j < cnt; ++j) {
-                        const float4 P = s_pos[j];
-                        const float4 c = s_col[j];
-                        const float fc = (fi >= c.w) ? s_fc2[j] : P.x;
-                        float dx, dy;
-                        pixel_offset(fi, fj, fc, P, dx, dy);
-                        const float p = gauss_exponent(s_con[j], dx, dy);
-                        if (p < kLog2AlphaMin) continue;
-                        const float alpha = fminf(kAlphaMax, exp2f(p));
-                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                        if (Tn < kTMin) { done = true; tested = b0 + j + 1; break; }
-                        const float w = __fmul_rn(alpha, T);
-                        C0 = __fmaf_rn(c.x, w, C0);
-                        C1 = __fmaf_rn(c.y, w, C1);
-                        C2 = __fmaf_rn(c.z, w, C2);
-                        T = Tn;
-                        last = b0 + j + 1;
-                        ++blended;
+                    const float fsplit = s_col[j].w, fc2 = s_fc2[j];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const float fi = fi0 + (float)k;
+                        const float dx = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), P.z);
+                        pk[k] = __fmaf_rn(__fmaf_rn(K.x, dx, Bdy), dx, rr);
                     }
                 }
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) any |= (!done[k]) & (pk[k] >= kLog2AlphaMin);
+                if (!any) continue;
+                const float4 c = s_col[j];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (done[k] || pk[k] < kLog2AlphaMin) continue;
+                    const float alpha = fminf(kAlphaMax, exp2f(pk[k]));
+                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                    if (Tn < kTMin) {
+                        done[k] = true;
+                        tested[k] = b0 + j + 1;
+                        --alive;
+                        continue;
+                    }
+                    const float w = __fmul_rn(alpha, T[k]);
+                    C0[k] = __fmaf_rn(c.x, w, C0[k]);
+                    C1[k] = __fmaf_rn(c.y, w, C1[k]);
+                    C2[k] = __fmaf_rn(c.z, w, C2[k]);
+                    T[k] = Tn;
+                    last[k] = b0 + j + 1;
+                    ++blended;
+                }
             }
-            if (__syncthreads_count(!done) == 0) break;
+            if (__syncthreads_count(alive > 0) == 0) break;
         }
         if (inside) {
             const int HW = V.W * V.H;
-            const int pix = y * V.W + x;
             float* img = a.images[v];
-            img[pix] = __fmaf_rn(T, a.bg[0], C0);
-            img[HW + pix] = __fmaf_rn(T, a.bg[1], C1);
-            img[2 * HW + pix] = __fmaf_rn(T, a.bg[2], C2);
-            a.T_final[V.pix_base + pix] = T;
-            a.n_last[V.pix_base + pix] = (uint32_t)last;
-            if (a.user_T[v]) a.user_T[v][pix] = T;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int pix = y * V.W + xp + k;
+                img[pix] = __fmaf_rn(T[k], a.bg[0], C0[k]);
+                img[HW + pix] = __fmaf_rn(T[k], a.bg[1], C1[k]);
+                img[2 * HW + pix] = __fmaf_rn(T[k], a.bg[2], C2[k]);
+                a.T_final[V.pix_base + pix] = T[k];
+                a.n_last[V.pix_base + pix] = (uint32_t)last[k];
+                if (a.user_T[v]) a.user_T[v][pix] = T[k];
+                evals += (uint32_t)tested[k];
+            }
         }
-        evals += (uint32_t)tested;
     }
     unsigned long long ev = evals;
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
@@ -134,32 +155,40 @@ __global__ void __launch_bounds__(MAXT) k_render_fwd(FwdArgs a) {
 
 size_t render_fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4) + sizeof(float)); }
 
-template <int MAXT>
-static cudaError_t launch_fwd_t(const FwdArgs& a, int grid, cudaStream_t st) {
-    size_t sm = render_fwd_smem(a.batch);
-    k_render_fwd<MAXT><<<grid, a.tile_w * a.tile_h, sm, st>>>(a);
-    return cudaGetLastError();
+int pixels_per_thread(int tile_w, int tile_h, int want) {
+    const int area = tile_w * tile_h;
+    auto fits = [&](int p) { return tile_w % p == 0 && (area / p) % 32 == 0 && area / p <= 256; };
+    if (want != 0) return (want == 1 || want == 2 || want == 4) && fits(want) ? want : 0;
+    for (int p = 4; p >= 1; p >>= 1)
+        if (fits(p)) return p;
+    return 0;
 }
 
-int render_fwd_occupancy(int threads, int batch) {
+int render_fwd_occupancy(int tile_w, int tile_h, int batch, int ppt) {
+    if (ppt == 0) return 1;
+    const int threads = tile_w * tile_h / ppt;
+    const size_t sm = render_fwd_smem(batch);
     int nb = 0;
-    size_t sm = render_fwd_smem(batch);
     cudaError_t e;
-    if (threads <= 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<64>, threads, sm);
-    else if (threads <= 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<128>, threads, sm);
-    else if (threads <= 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<256>, threads, sm);
-    else if (threads <= 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<512>, threads, sm);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<1024>, threads, sm);
-    return e == cudaSuccess ? max(nb, 1) : 1;
+    switch (ppt) {
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<4>, threads, sm); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<2>, threads, sm); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<1>, threads, sm); break;
+    }
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 cudaError_t launch_render_fwd(const FwdArgs& a, int grid, cudaStream_t st) {
-    const int threads = a.tile_w * a.tile_h;
-    if (threads <= 64) return launch_fwd_t<64>(a, grid, st);
-    if (threads <= 128) return launch_fwd_t<128>(a, grid, st);
-    if (threads <= 256) return launch_fwd_t<256>(a, grid, st);
-    if (threads <= 512) return launch_fwd_t<512>(a, grid, st);
-    return launch_fwd_t<1024>(a, grid, st);
+    const int ppt = a.ppt;
+    if (ppt != 1 && ppt != 2 && ppt != 4) return cudaErrorInvalidValue;
+    const int threads = a.tile_w * a.tile_h / ppt;
+    const size_t sm = render_fwd_smem(a.batch);
+    switch (ppt) {
+        case 4: k_render_fwd<4><<<grid, threads, sm, st>>>(a); break;
+        case 2: k_render_fwd<2><<<grid, threads, sm, st>>>(a); break;
+        default: k_render_fwd<1><<<grid, threads, sm, st>>>(a); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace odgs

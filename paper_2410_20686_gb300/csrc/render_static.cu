@@ -73,6 +73,8 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     if (!(st.tile_w == 8 || st.tile_w == 16 || st.tile_w == 32) || st.tile_h < 1 ||
         st.tile_w * st.tile_h < 32 || st.tile_w * st.tile_h > 1024 || (st.tile_w * st.tile_h) % 32 != 0)
         return ODGS_ERR_INVALID_ARG;
+    st.pixels_per_thread = pixels_per_thread(st.tile_w, st.tile_h, st.pixels_per_thread);
+    if (st.pixels_per_thread == 0) return ODGS_ERR_INVALID_ARG;
     if (st.batch < 1 || st.batch > 256) return ODGS_ERR_INVALID_ARG;
     if (!(st.cov_dilation >= 0.f) || !(st.r_near >= 0.f) || !(st.r_far > st.r_near)) return ODGS_ERR_INVALID_ARG;
     const int W = view->width, H = view->height;
@@ -179,14 +181,14 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
         return ODGS_ERR_CUDA;
     FwdArgs f{};
     f.views = vd; f.n_views = 1; f.total_tiles = tiles; f.tile_w = st.tile_w; f.tile_h = st.tile_h;
-    f.batch = st.batch; f.n_items = (uint32_t)n; f.ranges = ranges; f.pair_vals = pv[rp];
+    f.batch = st.batch; f.ppt = st.pixels_per_thread; f.n_items = (uint32_t)n; f.ranges = ranges; f.pair_vals = pv[rp];
     f.rec_a = rec_a; f.rec_b = rec_b; f.rec_c = rec_c;
     f.images[0] = image; f.user_T[0] = final_T;
     f.T_final = T_final; f.n_last = n_last;
     for (int i = 0; i < 3; ++i) f.bg[i] = st.bg[i];
     f.hdr = hdr;
     // the work counter and the evaluation counters were zeroed by k_setup in this call
-    const int per_sm = render_fwd_occupancy(st.tile_w * st.tile_h, st.batch);
+    const int per_sm = render_fwd_occupancy(st.tile_w, st.tile_h, st.batch, st.pixels_per_thread);
     long long grid = (long long)num_sms * per_sm;
     if (grid > tiles) grid = tiles;
     if (launch_render_fwd(f, (int)(grid < 1 ? 1 : grid), strm) != cudaSuccess) return ODGS_ERR_CUDA;

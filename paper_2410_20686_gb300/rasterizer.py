@@ -26,6 +26,7 @@ class RenderSettings:
     bg: tuple = (0.0, 0.0, 0.0)
     recompute_lists: bool = False
     grad_accumulate: bool = False
+    pixels_per_thread: int = 0
 
     def c_struct(self, sh_coeffs: int) -> L.Settings:
         s = L.Settings()
@@ -35,6 +36,7 @@ class RenderSettings:
         s.bg[:] = [float(b) for b in self.bg]
         s.recompute_lists = int(bool(self.recompute_lists))
         s.grad_accumulate = int(bool(self.grad_accumulate))
+        s.pixels_per_thread = int(self.pixels_per_thread)
         return s
 
 
