@@ -350,12 +350,14 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     b.vals = pv[0];
     b.big = reinterpret_cast<uint2*>(w + c->L.big);
     b.num_sms = c->num_sms;
+    b.key_hist = reinterpret_cast<uint32_t*>(p + c->P.hist);
+    b.key_passes = radix_passes(c->geo.key_bits);
     if (launch_binning(b, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
     // 3. stable sort of the pairs by tile id
     int rp = 0;
     if (launch_radix_sort(pk, pv, &hdr->n_pairs_sort, c->pb_cap, c->geo.key_bits, reinterpret_cast<uint32_t*>(p + c->P.hist),
                           reinterpret_cast<uint32_t*>(p + c->P.ctr), reinterpret_cast<uint32_t*>(p + c->P.lb),
-                          &hdr->status, c->num_sms, st, &rp, &c->launches) != cudaSuccess)
+                          &hdr->status, c->num_sms, st, &rp, &c->launches, /*hist_ready=*/true) != cudaSuccess)
         return ODGS_ERR_CUDA;
     c->sorted_vals = pv[rp];
     // 4. per-tile ranges

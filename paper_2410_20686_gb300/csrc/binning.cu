@@ -85,46 +85,101 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __rest
     }
 }
 
+// Counts the tile-sort digits of one emitted key (shared-memory histogram of the block).
+__device__ __forceinline__ void count_digits(uint32_t key, uint32_t (*s_hist)[256], int passes) {
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xFFu], 1u);
+}
+
 // Writes the pairs of one row band: columns start .. start + cnt - 1 (mod tiles_x), lanes
 // [lane0, lane0 + nlanes) sharing the work.
 __device__ __forceinline__ void write_band(uint32_t row, int start, int cnt, int tiles_x, uint32_t idx,
                                            unsigned long long off, unsigned long long capacity, int lane0,
-                                           int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                           int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                           uint32_t (*s_hist)[256], int passes) {
     for (int k = lane0; k < cnt; k += nlanes) {
         const unsigned long long o = off + (unsigned long long)k;
         if (o < capacity) {
             int tx = start + k;
             if (tx >= tiles_x) tx -= tiles_x;
-            keys[o] = row + (uint32_t)tx;
+            const uint32_t key = row + (uint32_t)tx;
+            keys[o] = key;
             vals[o] = idx;
+            count_digits(key, s_hist, passes);
         }
     }
 }
 
-// Emits all pairs of one item from offset off; lanes [lane0, lane0 + nlanes) cooperate.
-__device__ __forceinline__ void emit_item(uint32_t idx, unsigned long long off, const float4* __restrict__ rec_a,
-                                          const float4* __restrict__ rec_b, const ViewDev* __restrict__ views,
-                                          int n_per_view, int tw, int th, unsigned long long capacity, int lane0,
-                                          int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    const ViewDev& V = views[idx / (uint32_t)n_per_view];
-    Footprint fp = make_footprint(rec_a[idx], rec_b[idx]);
+// Emits all pairs of one item from offset off, by one thread.
+__device__ __forceinline__ void emit_item_thread(uint32_t idx, unsigned long long off, const EmitArgs& a,
+                                                 uint32_t (*s_hist)[256]) {
+    const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+    Footprint fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
     int jlo, jhi;
     footprint_rows(fp, V.H, jlo, jhi);
     if (jlo > jhi) return;
+    const int th = a.tile_h;
     for (int ty = jlo / th; ty <= jhi / th; ++ty) {
         int start, cnt;
-        band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, tw, V.tiles_x, start, cnt);
+        band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, start, cnt);
         const uint32_t row = (uint32_t)V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x;
-        write_band(row, start, cnt, V.tiles_x, idx, off, capacity, lane0, nlanes, keys, vals);
+        write_band(row, start, cnt, V.tiles_x, idx, off, a.capacity, 0, 1, a.keys, a.vals, s_hist, a.key_passes);
         off += (unsigned long long)cnt;
+    }
+}
+
+// Emits all pairs of one item from offset off, by a whole warp: lanes compute the spans of 32
+// row bands at a time, then the warp writes band after band, 32 columns per step.
+__device__ __forceinline__ void emit_item_warp(uint32_t idx, unsigned long long off, const EmitArgs& a, int lane,
+                                               uint32_t (*s_hist)[256]) {
+    const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+    Footprint fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
+    int jlo, jhi;
+    footprint_rows(fp, V.H, jlo, jhi);
+    if (jlo > jhi) return;
+    const int th = a.tile_h;
+    const int ty0 = jlo / th, ty1 = jhi / th;
+    for (int g = ty0; g <= ty1; g += 32) {
+        const int ty = g + lane;
+        int start = 0, cnt = 0;
+        if (ty <= ty1)
+            band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, start, cnt);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned nz = __ballot_sync(0xffffffffu, cnt > 0);
+        while (nz) {
+            const int l = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const int c = __shfl_sync(0xffffffffu, cnt, l);
+            const int s0 = __shfl_sync(0xffffffffu, start, l);
+            const int e0 = __shfl_sync(0xffffffffu, excl, l);
+            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(g + l) * (uint32_t)V.tiles_x;
+            write_band(row, s0, c, V.tiles_x, idx, off + (unsigned long long)e0, a.capacity, lane, 32, a.keys,
+                       a.vals, s_hist, a.key_passes);
+        }
+        off += (unsigned long long)total;
+    }
+}
+
+__device__ __forceinline__ void flush_digits(uint32_t (*s_hist)[256], uint32_t* key_hist, int passes) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = s_hist[i >> 8][i & 255];
+        if (c) atomicAdd(key_hist + i, c);
     }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_carry;
+    __shared__ uint32_t s_hist[4][256];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t base = blockIdx.x * kScanTile;
+    for (int i = tid; i < 4 * 256; i += kScanThreads) s_hist[i >> 8][i & 255] = 0u;
     if (tid == 0) s_carry = a.block_offsets[blockIdx.x];
     __syncthreads();
     for (int round = 0; round < kScanItems; ++round) {
@@ -148,9 +203,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
         __syncthreads();
         if (tid == 0) s_carry += tot;
         // small items: one lane each
-        if (cnt > 0u && cnt <= 32u)
-            emit_item(idx, off, a.rec_a, a.rec_b, a.views, a.n_per_view, a.tile_w, a.tile_h, a.capacity, 0, 1,
-                      a.keys, a.vals);
+        if (cnt > 0u && cnt <= 32u) emit_item_thread(idx, off, a, s_hist);
         // large items: queued for k_emit_big (whole warps, dynamically scheduled). Depth order
         // clusters the nearest, largest Gaussians into the first blocks, so serving them here
         // would leave a few warps writing most of the pairs.
@@ -159,9 +212,13 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
             a.big[slot] = make_uint2(idx, (uint32_t)off);
         }
     }
+    flush_digits(s_hist, a.key_hist, a.key_passes);
 }
 
 __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
+    __shared__ uint32_t s_hist[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i >> 8][i & 255] = 0u;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t n_big = a.hdr->n_big;
     for (;;) {
@@ -170,9 +227,9 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= n_big) break;
         const uint2 e = a.big[i];
-        emit_item(e.x, (unsigned long long)e.y, a.rec_a, a.rec_b, a.views, a.n_per_view, a.tile_w, a.tile_h,
-                  a.capacity, lane, 32, a.keys, a.vals);
+        emit_item_warp(e.x, (unsigned long long)e.y, a, lane, s_hist);
     }
+    flush_digits(s_hist, a.key_hist, a.key_passes);
 }
 
 __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, const Header* __restrict__ hdr,
@@ -199,12 +256,15 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
     k_scan_blocks<<<1, 1024, 0, st>>>(a.block_sums, nb, a.hdr, a.capacity);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
+    if (nb == 0 && (e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
     if (nb > 0) {
         EmitArgs ea{};
         ea.sorted_idx = a.sorted_idx; ea.rect = a.rect; ea.rec_a = a.rec_a; ea.rec_b = a.rec_b; ea.views = a.views;
         ea.n_per_view = a.n_per_view; ea.n_items = a.n_items; ea.tile_w = a.tile_w; ea.tile_h = a.tile_h;
         ea.block_offsets = a.block_sums; ea.capacity = a.capacity; ea.keys = a.keys; ea.vals = a.vals;
         ea.big = a.big; ea.hdr = a.hdr;
+        ea.key_hist = a.key_hist; ea.key_passes = a.key_passes;
+        if ((e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
         k_emit<<<nb, kScanThreads, 0, st>>>(ea);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_emit_big<<<a.num_sms * 4, 256, 0, st>>>(ea);

@@ -51,6 +51,8 @@ struct BinArgs {
     uint32_t *keys, *vals;
     uint2* big;  // [n_items] queue of (item, offset) with more than 32 pairs
     int num_sms;
+    uint32_t* key_hist;  // [passes][256] digit histograms of the emitted tile ids (zeroed here)
+    int key_passes;
 };
 
 struct EmitArgs {
@@ -66,6 +68,8 @@ struct EmitArgs {
     uint32_t *keys, *vals;
     uint2* big;
     Header* hdr;
+    uint32_t* key_hist;
+    int key_passes;
 };
 
 struct FwdArgs {
@@ -107,7 +111,7 @@ int radix_passes(int bits);
 size_t radix_lookback_words(size_t max_items);
 cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
-                              cudaStream_t st, int* result_buf, int* launches);
+                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready = false);
 
 int scan_blocks_for(uint32_t n_items);
 cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches);

@@ -6,7 +6,7 @@
 // stable sort of 64-bit (tile | depth) keys, with far fewer bytes moved.
 //
 // One histogram kernel counts the digits of all passes in a single read of the keys; each
-// pass is then one "onesweep" kernel (Adinets & Merrill 2022): a CTA ranks a 4096-key tile in
+// pass is then one "onesweep" kernel (Adinets & Merrill 2022): a CTA ranks a 2048-key tile in
 // shared memory (warp-level match ranking keeps it stable), publishes its per-digit counts,
 // obtains the exclusive prefix of all earlier tiles by decoupled look-back, and writes its keys
 // digit-run by digit-run (coalesced). Look-back waits are bounded: a CTA that gives up sets
@@ -18,7 +18,7 @@ namespace odgs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
@@ -202,21 +202,24 @@ size_t radix_lookback_words(size_t max_items) {
 }
 
 // Sorts (k[0], v[0]) by key bits [0, bits); returns the buffer index (0 or 1) that holds the
-// result. scratch: hist [4 * 256] + tile counters [4] + lookback [radix_lookback_words].
+// result. scratch: hist [4 * 256] + tile counters [4] + lookback [radix_lookback_words]. With
+// hist_ready the digit histograms of all passes are already in hist (counted by the producer).
 cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
-                              cudaStream_t st, int* result_buf, int* launches) {
+                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready) {
     const int passes = radix_passes(bits);
     *result_buf = 0;
     if (passes == 0 || max_items == 0) return cudaSuccess;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * kRadix, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(tile_ctrs, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return e;
-    int hblocks = (int)min((max_items + 255) / 256, (size_t)num_sms * 8);
-    hblocks = max(hblocks, 1);
-    k_radix_hist<<<hblocks, 256, 0, st>>>(k[0], n_ptr, 0, passes, hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *launches += 1;
+    if (!hist_ready) {
+        if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * kRadix, st)) != cudaSuccess) return e;
+        int hblocks = (int)min((max_items + 255) / 256, (size_t)num_sms * 8);
+        hblocks = max(hblocks, 1);
+        k_radix_hist<<<hblocks, 256, 0, st>>>(k[0], n_ptr, 0, passes, hist);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 1;
+    }
     const size_t lb_words = radix_lookback_words(max_items);
     const int tiles = (int)(lb_words / kRadix);
     int cur = 0;

@@ -172,10 +172,11 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     b.n_items = (uint32_t)n; b.block_sums = block_sums; b.hdr = hdr; b.capacity = cap;
     b.keys = pk[0]; b.vals = pv[0];
     b.big = big; b.num_sms = num_sms;
+    b.key_hist = p_hist; b.key_passes = radix_passes(key_bits);
     if (launch_binning(b, strm, &launches) != cudaSuccess) return ODGS_ERR_CUDA;
     int rp = 0;
     if (launch_radix_sort(pk, pv, &hdr->n_pairs_sort, cap, key_bits, p_hist, p_ctr, p_lb, &hdr->status, num_sms,
-                          strm, &rp, &launches) != cudaSuccess)
+                          strm, &rp, &launches, /*hist_ready=*/true) != cudaSuccess)
         return ODGS_ERR_CUDA;
     if (launch_tile_ranges(pk[rp], hdr, ranges, tiles, cap, num_sms, strm, &launches) != cudaSuccess)
         return ODGS_ERR_CUDA;
