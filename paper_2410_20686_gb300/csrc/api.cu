@@ -44,7 +44,7 @@ Layout make_layout(size_t items, const Geometry& g) {
     L.rec_a = take(sizeof(float4) * items);
     L.rec_b = take(sizeof(float4) * items);
     L.rec_c = take(sizeof(float4) * items);
-    L.rect = take(sizeof(uint2) * items);
+    L.rect = take(sizeof(uint4) * items);
     L.dkey0 = take(sizeof(uint32_t) * items);
     L.dkey1 = take(sizeof(uint32_t) * items);
     L.dval0 = take(sizeof(uint32_t) * items);
@@ -242,7 +242,7 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.rec_a = reinterpret_cast<float4*>(w + c->L.rec_a);
     a.rec_b = reinterpret_cast<float4*>(w + c->L.rec_b);
     a.rec_c = reinterpret_cast<float4*>(w + c->L.rec_c);
-    a.rect = reinterpret_cast<uint2*>(w + c->L.rect);
+    a.rect = reinterpret_cast<uint4*>(w + c->L.rect);
     a.dkey = reinterpret_cast<uint32_t*>(w + c->L.dkey0);
     a.dval = reinterpret_cast<uint32_t*>(w + c->L.dval0);
     a.hdr = hdr;
@@ -335,7 +335,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     uint32_t* pv[2] = {reinterpret_cast<uint32_t*>(p + c->P.vals0), reinterpret_cast<uint32_t*>(p + c->P.vals1)};
     BinArgs b{};
     b.sorted_idx = dv[rb];
-    b.rect = reinterpret_cast<const uint2*>(w + c->L.rect);
+    b.rect = reinterpret_cast<const uint4*>(w + c->L.rect);
     b.rec_a = reinterpret_cast<const float4*>(w + c->L.rec_a);
     b.rec_b = reinterpret_cast<const float4*>(w + c->L.rec_b);
     b.tile_w = c->s.tile_w;

@@ -19,7 +19,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t rect_tiles(uint2 r) { return r.y; }
+__device__ __forceinline__ uint32_t rect_tiles(uint4 r) { return r.y; }
 
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* s) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -32,14 +32,14 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_count_blocks(const uint32_t* __restrict__ sorted_idx,
-                                                              const uint2* __restrict__ rect, uint32_t n_items,
+                                                              const uint4* __restrict__ rect, uint32_t n_items,
                                                               unsigned long long* __restrict__ block_sums) {
     __shared__ unsigned long long s[kScanThreads / 32];
     const uint32_t base = blockIdx.x * kScanTile;
     unsigned long long c = 0ull;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
         uint32_t k = base + i;
-        if (k < n_items) c += rect_tiles(rect[sorted_idx[k]]);
+        if (k < n_items) c += __ldg(&rect[sorted_idx[k]].y);
     }
     c = block_sum_u64(c, s);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = c;
@@ -85,40 +85,69 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __rest
     }
 }
 
-// Counts the tile-sort digits of one emitted key (shared-memory histogram of the block).
-__device__ __forceinline__ void count_digits(uint32_t key, uint32_t (*s_hist)[256], int passes) {
-    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xFFu], 1u);
-}
-
-// Writes the pairs of one row band: columns start .. start + cnt - 1 (mod tiles_x), lanes
-// [lane0, lane0 + nlanes) sharing the work.
-__device__ __forceinline__ void write_band(uint32_t row, int start, int cnt, int tiles_x, uint32_t idx,
-                                           unsigned long long off, unsigned long long capacity, int lane0,
-                                           int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                           uint32_t (*s_hist)[256], int passes) {
-    for (int k = lane0; k < cnt; k += nlanes) {
-        const unsigned long long o = off + (unsigned long long)k;
-        if (o < capacity) {
-            int tx = start + k;
-            if (tx >= tiles_x) tx -= tiles_x;
-            const uint32_t key = row + (uint32_t)tx;
-            keys[o] = key;
-            vals[o] = idx;
-            count_digits(key, s_hist, passes);
+// Counts the tile-sort digits of the keys key0 .. key0 + cnt - 1 (a contiguous run) in the block's
+// shared histogram. Lanes [lane0, lane0 + nlanes) share the low digit (distinct bins, one atomic
+// per key); the first lane adds the higher digits one constant-digit segment at a time, so a row
+// of consecutive tiles costs one atomic per higher digit instead of one per key.
+__device__ __forceinline__ void count_run(uint32_t key0, int cnt, uint32_t (*s_hist)[256], int passes, int lane0,
+                                          int nlanes) {
+    if (cnt <= 0) return;
+    for (int k = lane0; k < cnt; k += nlanes) atomicAdd(&s_hist[0][(key0 + (uint32_t)k) & 0xFFu], 1u);
+    if (lane0 != 0) return;
+    const uint32_t end = key0 + (uint32_t)cnt;
+    for (int p = 1; p < passes; ++p) {
+        const int sh = 8 * p;
+        uint32_t k = key0;
+        while (k < end) {
+            const uint32_t seg_end = min(end, ((k >> sh) + 1u) << sh);
+            atomicAdd(&s_hist[p][(k >> sh) & 0xFFu], seg_end - k);
+            k = seg_end;
         }
     }
 }
 
-// Emits all pairs of one item from offset off, by one thread.
-__device__ __forceinline__ void emit_item_thread(uint32_t idx, unsigned long long off, const EmitArgs& a,
+// Writes the pairs of one row band: columns start .. start + cnt - 1 (mod tiles_x), lanes
+// [lane0, lane0 + nlanes) sharing the work, and counts their tile-sort digits. Pairs at or
+// beyond the capacity are neither written nor counted.
+__device__ __forceinline__ void write_band(uint32_t row, int start, int cnt, int tiles_x, uint32_t idx,
+                                           unsigned long long off, unsigned long long capacity, int lane0,
+                                           int nlanes, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                           uint32_t (*s_hist)[256], int passes) {
+    if (off >= capacity) return;
+    if ((unsigned long long)cnt > capacity - off) cnt = (int)(capacity - off);
+    for (int k = lane0; k < cnt; k += nlanes) {
+        const unsigned long long o = off + (unsigned long long)k;
+        int tx = start + k;
+        if (tx >= tiles_x) tx -= tiles_x;
+        keys[o] = row + (uint32_t)tx;
+        vals[o] = idx;
+    }
+    // digit counts of the (at most two, seam-wrapped) runs of consecutive keys
+    const int first = min(cnt, tiles_x - start);
+    count_run(row + (uint32_t)start, first, s_hist, passes, lane0, nlanes);
+    count_run(row, cnt - first, s_hist, passes, lane0, nlanes);
+}
+
+// Emits all pairs of one item from offset off, by one thread. The spans of the item's first two
+// row bands were stored by the preprocess; further bands are recomputed (same functions).
+__device__ __forceinline__ void emit_item_thread(uint32_t idx, uint4 rc, unsigned long long off, const EmitArgs& a,
                                                  uint32_t (*s_hist)[256]) {
     const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+    const int ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
+    const int th = a.tile_h;
+    const uint32_t spans[2] = {rc.z, rc.w};
+    for (int b = 0; b < nb && b < 2; ++b) {
+        const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
+        const int cnt = (int)(spans[b] >> 16);
+        write_band(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, off, a.capacity, 0, 1, a.keys, a.vals,
+                   s_hist, a.key_passes);
+        off += (unsigned long long)cnt;
+    }
+    if (nb <= 2) return;
     Footprint fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
     int jlo, jhi;
     footprint_rows(fp, V.H, jlo, jhi);
-    if (jlo > jhi) return;
-    const int th = a.tile_h;
-    for (int ty = jlo / th; ty <= jhi / th; ++ty) {
+    for (int ty = ty0 + 2; ty < ty0 + nb; ++ty) {
         int start, cnt;
         band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, start, cnt);
         const uint32_t row = (uint32_t)V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x;
@@ -132,14 +161,27 @@ __device__ __forceinline__ void emit_item_thread(uint32_t idx, unsigned long lon
 __device__ __forceinline__ void emit_item_warp(uint32_t idx, unsigned long long off, const EmitArgs& a, int lane,
                                                uint32_t (*s_hist)[256]) {
     const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+    const uint4 rc = a.rect[idx];
+    const int th = a.tile_h;
+    if ((rc.x >> 16) <= 2u) {  // spans stored by the preprocess
+        const int ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
+        const uint32_t spans[2] = {rc.z, rc.w};
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
+            const int cnt = (int)(spans[b] >> 16);
+            write_band(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, off, a.capacity, lane, 32, a.keys, a.vals,
+                       s_hist, a.key_passes);
+            off += (unsigned long long)cnt;
+        }
+        return;
+    }
     Footprint fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
     int jlo, jhi;
     footprint_rows(fp, V.H, jlo, jhi);
     if (jlo > jhi) return;
-    const int th = a.tile_h;
     const int ty0 = jlo / th, ty1 = jhi / th;
-    for (int g = ty0; g <= ty1; g += 32) {
-        const int ty = g + lane;
+    for (int gq = ty0; gq <= ty1; gq += 32) {
+        const int ty = gq + lane;
         int start = 0, cnt = 0;
         if (ty <= ty1)
             band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, start, cnt);
@@ -157,9 +199,9 @@ __device__ __forceinline__ void emit_item_warp(uint32_t idx, unsigned long long 
             const int c = __shfl_sync(0xffffffffu, cnt, l);
             const int s0 = __shfl_sync(0xffffffffu, start, l);
             const int e0 = __shfl_sync(0xffffffffu, excl, l);
-            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(g + l) * (uint32_t)V.tiles_x;
-            write_band(row, s0, c, V.tiles_x, idx, off + (unsigned long long)e0, a.capacity, lane, 32, a.keys,
-                       a.vals, s_hist, a.key_passes);
+            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(gq + l) * (uint32_t)V.tiles_x;
+            write_band(row, s0, c, V.tiles_x, idx, off + (unsigned long long)e0, a.capacity, lane, 32, a.keys, a.vals,
+                       s_hist, a.key_passes);
         }
         off += (unsigned long long)total;
     }
@@ -185,7 +227,8 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
     for (int round = 0; round < kScanItems; ++round) {
         const uint32_t k = base + (uint32_t)(round * kScanThreads + tid);
         const uint32_t idx = k < a.n_items ? a.sorted_idx[k] : 0u;
-        const uint32_t cnt = k < a.n_items ? a.rect[idx].y : 0u;
+        const uint4 rc = k < a.n_items ? a.rect[idx] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t cnt = rc.y;
         // block-wide exclusive scan of the counts of this round (items in depth order)
         unsigned long long x = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -203,13 +246,16 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
         __syncthreads();
         if (tid == 0) s_carry += tot;
         // small items: one lane each
-        if (cnt > 0u && cnt <= 32u) emit_item_thread(idx, off, a, s_hist);
+        if (cnt > 0u && cnt <= 32u) emit_item_thread(idx, rc, off, a, s_hist);
         // large items: queued for k_emit_big (whole warps, dynamically scheduled). Depth order
         // clusters the nearest, largest Gaussians into the first blocks, so serving them here
         // would leave a few warps writing most of the pairs.
-        if (cnt > 32u) {
-            const uint32_t slot = atomicAdd(&a.hdr->n_big, 1u);
-            a.big[slot] = make_uint2(idx, (uint32_t)off);
+        const unsigned bigm = __ballot_sync(0xffffffffu, cnt > 32u);
+        if (bigm) {  // one queue reservation per warp
+            uint32_t base_slot = 0u;
+            if (lane == __ffs(bigm) - 1) base_slot = atomicAdd(&a.hdr->n_big, (uint32_t)__popc(bigm));
+            base_slot = __shfl_sync(0xffffffffu, base_slot, __ffs(bigm) - 1);
+            if (cnt > 32u) a.big[base_slot + __popc(bigm & ((1u << lane) - 1u))] = make_uint2(idx, (uint32_t)off);
         }
     }
     flush_digits(s_hist, a.key_hist, a.key_passes);
@@ -221,11 +267,9 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t n_big = a.hdr->n_big;
-    for (;;) {
-        uint32_t i = 0;
-        if (lane == 0) i = atomicAdd(&a.hdr->big_next, 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if (i >= n_big) break;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    // static round-robin over the queue: no shared counter to contend on
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_big; i += nwarps) {
         const uint2 e = a.big[i];
         emit_item_warp(e.x, (unsigned long long)e.y, a, lane, s_hist);
     }
@@ -267,7 +311,7 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
         if ((e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
         k_emit<<<nb, kScanThreads, 0, st>>>(ea);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_emit_big<<<a.num_sms * 4, 256, 0, st>>>(ea);
+        k_emit_big<<<a.num_sms * 8, 256, 0, st>>>(ea);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 2;
     }

@@ -22,7 +22,7 @@ struct PreArgs {
     const float4* trig;
     Settings st;
     float4 *rec_a, *rec_b, *rec_c;
-    uint2* rect;
+    uint4* rect;  // (ty0 | bands << 16, tiles, span of band 0, span of band 1); span = start | count << 16
     uint32_t *dkey, *dval;
     Header* hdr;
 };
@@ -39,7 +39,7 @@ struct PreBwdArgs {
 
 struct BinArgs {
     const uint32_t* sorted_idx;
-    const uint2* rect;
+    const uint4* rect;
     const float4 *rec_a, *rec_b;
     int tile_w, tile_h;
     const ViewDev* views;
@@ -57,7 +57,7 @@ struct BinArgs {
 
 struct EmitArgs {
     const uint32_t* sorted_idx;
-    const uint2* rect;
+    const uint4* rect;
     const float4 *rec_a, *rec_b;
     const ViewDev* views;
     int n_per_view;

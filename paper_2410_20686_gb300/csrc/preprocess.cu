@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
         for (int v = 0; v < a.n_views; ++v) {
             const ViewDev& V = a.views[v];
             const size_t item = (size_t)v * a.n + g;
-            uint2 rect = make_uint2(0u, 0u);
+            uint4 rect = make_uint4(0u, 0u, 0u, 0u);
             uint32_t key = 0xFFFFFFFFu;
             const float r = depth_key(V, m0, m1, m2);
             bool ok = (r > a.st.r_near) && (r < a.st.r_far) && (Qalpha > 0.f);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
                     Footprint fp = make_footprint(ra, rb);
                     int jlo, jhi;
                     footprint_rows(fp, V.H, jlo, jhi);
-                    uint32_t count = 0u;
+                    uint32_t count = 0u, span[2] = {0u, 0u};
                     const int th = a.st.tile_h;
                     const int ty0 = jlo / th, ty1 = jhi / th;
                     if (jlo <= jhi) {
@@ -293,10 +293,11 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
                             band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.st.tile_w,
                                          V.tiles_x, st0, cnt);
                             count += (uint32_t)cnt;
+                            if (ty - ty0 < 2) span[ty - ty0] = (uint32_t)st0 | ((uint32_t)cnt << 16);
                         }
                     }
                     if (count > 0u) {
-                        rect = make_uint2((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count);
+                        rect = make_uint4((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count, span[0], span[1]);
                         local_pairs += count;
                         key = __float_as_uint(r);
                         // view-dependent colour: max(0, sum_k sh_k Y_k(d) + 0.5), d from the

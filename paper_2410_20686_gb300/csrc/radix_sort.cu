@@ -18,7 +18,8 @@ namespace odgs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 8;
+constexpr int kSortItemsMax = 16;  // 4096 keys per CTA for large sorts, 2048 below kLargeSort
+constexpr size_t kLargeSort = 4u << 20;
 constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
@@ -75,7 +76,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_
     return wpre + x - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+template <int kSortItems>
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          const uint32_t* __restrict__ n_ptr, int shift,
                                                          int bits, const uint32_t* __restrict__ hist,
@@ -108,13 +110,22 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint32_t* __res
         key[i] = valid ? kin[idx] : 0u;
         val[i] = valid ? vin[idx] : 0u;
     }
-    // stable warp-level ranking: items are ordered by (warp, i, lane)
+    // stable warp-level ranking: items are ordered by (warp, i, lane). The lanes holding the
+    // same digit are found with one ballot per digit bit (bit-split multisplit).
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
         const bool valid = idx < n;
         const uint32_t d = (key[i] >> shift) & mask;
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (b < bits) {
+                const bool bit = (d >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
+        }
         const uint32_t before = valid ? s_warp_hist[warp][d] : 0u;
         __syncwarp();
         if (valid && lane == (uint32_t)(__ffs(peers) - 1)) s_warp_hist[warp][d] = before + (uint32_t)__popc(peers);
@@ -196,8 +207,10 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint32_t* __res
 
 int radix_passes(int bits) { return (bits + 7) / 8; }
 
+// Look-back words for the smaller (2048-key) tile, which needs the most.
 size_t radix_lookback_words(size_t max_items) {
-    size_t tiles = (max_items + kSortThreads * kSortItems - 1) / (kSortThreads * kSortItems);
+    const size_t per = kSortThreads * (kSortItemsMax / 2);
+    size_t tiles = (max_items + per - 1) / per;
     return (tiles ? tiles : 1) * kRadix;
 }
 
@@ -220,15 +233,31 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
     }
+    static bool carveout_set = false;  // all of the SM's shared memory for the onesweep CTAs
+    if (!carveout_set) {
+        cudaFuncSetAttribute(k_onesweep<kSortItemsMax>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_onesweep<kSortItemsMax / 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        carveout_set = true;
+    }
+    const bool large = max_items >= kLargeSort;
+    const int per_cta = kSortThreads * (large ? kSortItemsMax : kSortItemsMax / 2);
     const size_t lb_words = radix_lookback_words(max_items);
-    const int tiles = (int)(lb_words / kRadix);
+    const int tiles = (int)((max_items + per_cta - 1) / per_cta);
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int pbits = min(8, bits - shift);
         if ((e = cudaMemsetAsync(lookback, 0, sizeof(uint32_t) * lb_words, st)) != cudaSuccess) return e;
-        k_onesweep<<<tiles, kSortThreads, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits,
-                                                   hist + p * kRadix, lookback, tile_ctrs + p, status);
+        if (large)
+            k_onesweep<kSortItemsMax><<<max(tiles, 1), kSortThreads, 0, st>>>(
+                k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, hist + p * kRadix, lookback,
+                tile_ctrs + p, status);
+        else
+            k_onesweep<kSortItemsMax / 2><<<max(tiles, 1), kSortThreads, 0, st>>>(
+                k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, hist + p * kRadix, lookback,
+                tile_ctrs + p, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
         cur ^= 1;

@@ -123,7 +123,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     float4* rec_a = reinterpret_cast<float4*>(take(sizeof(float4) * n));
     float4* rec_b = reinterpret_cast<float4*>(take(sizeof(float4) * n));
     float4* rec_c = reinterpret_cast<float4*>(take(sizeof(float4) * n));
-    uint2* rect = reinterpret_cast<uint2*>(take(sizeof(uint2) * n));
+    uint4* rect = reinterpret_cast<uint4*>(take(sizeof(uint4) * n));
     uint32_t* dk[2] = {reinterpret_cast<uint32_t*>(take(4 * n)), reinterpret_cast<uint32_t*>(take(4 * n))};
     uint32_t* dv[2] = {reinterpret_cast<uint32_t*>(take(4 * n)), reinterpret_cast<uint32_t*>(take(4 * n))};
     unsigned long long* block_sums =
