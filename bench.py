@@ -34,7 +34,7 @@ CPU_SAMPLE_PIXELS = 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--tile", type=str, default="16x16")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the blend kernels (0 = auto)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 16-view batched measurement")
+    ap.add_argument("--batched-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -62,7 +64,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -204,6 +206,67 @@ def run_reference(args):
                             "sample": "each step: 256 seeded pixels, forward + adjoint, extrapolated to the full frame"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ batched views (config 3)
+
+BATCHED_WORKLOAD = ("config3: 500,000 shared Gaussians (SH3), 16 ERP views (4x512x256, 4x1024x512, "
+                    "8x2048x1024) on a 3 m path with random yaw, fwd+bwd with L1 loss, gradients of all "
+                    "views summed into one buffer")
+
+
+def run_batched(dev, rs, steps, warmup):
+    """views/s of one CUDA-graph-replayed 16-view frame vs the same views one frame at a time."""
+    import torch
+    from dataclasses import replace
+    from paper_2410_20686_gb300 import scenes as S
+    from paper_2410_20686_gb300.graph import GraphedFrame, l1_grad
+    from paper_2410_20686_gb300.rasterizer import Rasterizer
+
+    sc = S.config3()
+    params = [torch.tensor(a, device=dev) for a in (sc.means, sc.scales, sc.quats, sc.opacity, sc.sh)]
+    targets = [torch.tensor(t, device=dev) for t in S.target_images(sc, 3)]
+    V = len(sc.views)
+    gf = GraphedFrame(params, sc.views, targets, rs)
+    for _ in range(warmup):
+        gf.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gf.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_b = e0.elapsed_time(e1) / 1e3 / steps
+    assert gf.status() == 0
+    # the same views, one frame each (same kernels, no graph); gradients summed over the views
+    rast = Rasterizer(dev, capacity_mode="query", headroom=1.3)
+    grads = {k: torch.empty_like(t) for k, t in zip(("means", "scales", "quats", "opacity", "sh"), params)}
+    acc = replace(rs, grad_accumulate=True)
+
+    def single_round():
+        for i, (v, tg) in enumerate(zip(sc.views, targets)):
+            r = rs if i == 0 else acc
+            imgs, _ = rast.forward(*params, [v], r, want_T=False)
+            _, gi = l1_grad(imgs, [tg])
+            rast.backward(gi, grads)
+
+    single_round()  # sizes the buffers for the largest view
+    torch.cuda.synchronize(dev)
+    rast.capacity_mode = "fixed"
+    for _ in range(warmup):
+        single_round()
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(steps):
+        single_round()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_s = e0.elapsed_time(e1) / 1e3 / steps
+    assert rast.status() == 0
+    return {"workload": BATCHED_WORKLOAD, "views_per_s": V / t_b, "single_views_per_s": V / t_s,
+            "speedup": t_s / t_b, "ms_per_frame": t_b * 1e3, "ms_per_views_one_at_a_time": t_s * 1e3,
+            "kernel_launches_per_frame": gf.launches, "steps": steps, "per_gpu": True}
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -361,6 +424,8 @@ def run_ours(args):
            "roofline": roofline, "kernels_ms": kern, "gpu_launches": launches_per_step * K, "clocks": clocks}
     if e2e:
         out["e2e"] = e2e
+    if not args.no_batched:
+        out["batched"] = run_batched(dev, rs, args.batched_steps, args.warmup)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(out), flush=True)
