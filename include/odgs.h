@@ -73,7 +73,9 @@ typedef struct {
     float cov_dilation; /* added to both diagonals of Sigma_2D (px^2); e.g. 0.3          */
     float r_near, r_far;/* spherical-shell culling radii (Sec. 3.2); e.g. 0.2, 1e4       */
     float bg[3];        /* background colour blended with the final transmittance        */
-    int recompute_lists;/* 1: odgs_render_bwd re-runs preprocess + bin_sort itself        */
+    int recompute_lists;/* 1: odgs_render_bwd rebuilds the tile lists (odgs_bin_sort) in the
+                           pair buffer last given to odgs_bin_sort, which the caller may
+                           reuse for other frames between the forward and backward passes */
     int grad_accumulate;/* 1: gradients are added (+=) to the output arrays; 0: written  */
     int pixels_per_thread; /* blend kernels: pixels of one row per thread, 1, 2 or 4;
                               0 -> the largest that divides tile_w while tile_w * tile_h /
@@ -132,7 +134,8 @@ odgs_status odgs_render_fwd(odgs_ctx *ctx, float *const *images, float *const *f
 /* Backward pass, part 1: reverse of the blend of Eq. 3 per pixel (back to front from each
  * pixel's last blended Gaussian), accumulating per (view, Gaussian) the gradients w.r.t. its ERP
  * mean, conic, opacity and colour in the workspace. dL_dimages[v]: device [3][H][W] float32.
- * With recompute_lists = 1 it first re-runs odgs_preprocess and odgs_bin_sort (identical lists). */
+ * With recompute_lists = 1 it first rebuilds the tile lists (identical to the forward's) from the
+ * records kept in the workspace, into the pair buffer last given to odgs_bin_sort. */
 odgs_status odgs_render_bwd(odgs_ctx *ctx, const float *const *dL_dimages, void *stream);
 
 /* Backward pass, part 2: chain rule from the accumulated screen-space gradients to the Gaussian

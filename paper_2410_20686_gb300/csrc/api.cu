@@ -432,10 +432,10 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
         if (!dL[v]) return ODGS_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (c->s.recompute_lists) {
-        // the tile lists were not kept: rebuild them (deterministically identical)
-        odgs_status r = run_preprocess(c, st);
-        if (r != ODGS_OK) return r;
-        r = run_bin_sort(c, st);
+        // the tile lists were not kept (the pair buffer may have served other frames since
+        // odgs_render_fwd): rebuild them from the per-item records, which the workspace still
+        // holds. The binning is deterministic, so the lists are identical to the forward's.
+        odgs_status r = run_bin_sort(c, st);
         if (r != ODGS_OK) return r;
     }
     uint8_t* w = c->ws;

@@ -86,3 +86,57 @@ class GraphedFrame:
     def status(self) -> int:
         """Device status bits of the last replay (synchronises)."""
         return self.rast.status()
+
+
+class GroupedFrame:
+    """One fwd+bwd frame whose views are rendered in groups that share one pair buffer.
+
+    Each group's tile lists are rebuilt in its backward pass (``recompute_lists``), so the pair
+    buffer only has to hold the largest group's lists, not the whole frame's. Gradients of all
+    groups are summed into ``self.grads``. Runs eagerly (no graph).
+    """
+
+    def __init__(self, params, views, targets, settings: RenderSettings = None, group_size: int = 1,
+                 headroom: float = 1.3, loss_fn=l1_grad):
+        from dataclasses import replace
+        from .rasterizer import PairPool
+        self.params = list(params)
+        self.views = list(views)
+        self.targets = list(targets)
+        base = settings or RenderSettings()
+        self.loss_fn = loss_fn
+        dev = self.params[0].device
+        self.groups = [self.views[i:i + group_size] for i in range(0, len(self.views), group_size)]
+        self.settings = [replace(base, recompute_lists=True, grad_accumulate=(i > 0)) for i in range(len(self.groups))]
+        self.pool = PairPool(dev)
+        self.rasts = [Rasterizer(dev, capacity_mode="fixed", pairs=self.pool) for _ in self.groups]
+        self.grads = {k: torch.empty_like(t) for k, t in zip(_GRAD_NAMES, self.params)}
+        # size the shared pair buffer for the largest group (one synchronising query per group)
+        need = 0
+        for r, vs, st in zip(self.rasts, self.groups, self.settings):
+            r.preprocess(*self.params, vs, st)
+            need = max(need, r.query_pairs())
+        for r in self.rasts:
+            r.reserve_pairs(int(need * headroom) + 1024)
+
+    def step(self):
+        images = []
+        for r, vs, st in zip(self.rasts, self.groups, self.settings):
+            imgs, _ = r.forward(*self.params, vs, st, want_T=False)
+            images += imgs
+        loss, gi = self.loss_fn(images, self.targets)
+        k = 0
+        for r, vs in zip(self.rasts, self.groups):
+            r.backward(gi[k:k + len(vs)], self.grads)
+            k += len(vs)
+        self.images = images
+        return loss
+
+    def status(self) -> int:
+        bits = 0
+        for r in self.rasts:
+            bits |= r.status()
+        return bits
+
+    def pair_buffer_bytes(self) -> int:
+        return int(self.pool.tensor.numel()) if self.pool.tensor is not None else 0

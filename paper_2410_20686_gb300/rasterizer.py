@@ -54,6 +54,24 @@ def _views_array(views):
     return arr
 
 
+class PairPool:
+    """A pair buffer shared by several rasterizers whose tile lists need not coexist (with
+    ``recompute_lists`` each backward pass rebuilds its lists), so a frame split into view groups
+    needs pair memory for its largest group only."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.tensor = None
+        self.capacity = 0
+
+    def reserve(self, lib, capacity: int, device):
+        need = C.c_size_t()
+        L.check(lib.odgs_pair_buffer_size(int(capacity), C.byref(need)), "odgs_pair_buffer_size")
+        if self.tensor is None or self.tensor.numel() < need.value:
+            self.tensor = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=device)
+        self.capacity = max(self.capacity, int(capacity))
+
+
 class Rasterizer:
     """One frame of state (a C ``odgs_ctx``) plus its device buffers.
 
@@ -62,7 +80,7 @@ class Rasterizer:
     the pair buffer as sized so far (``reserve_pairs``), which CUDA-graph capture requires.
     """
 
-    def __init__(self, device=None, capacity_mode: str = "query", headroom: float = 1.25):
+    def __init__(self, device=None, capacity_mode: str = "query", headroom: float = 1.25, pairs: PairPool = None):
         self.lib = L.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
@@ -72,8 +90,7 @@ class Rasterizer:
         self.capacity_mode = capacity_mode
         self.headroom = headroom
         self.ws = None
-        self.pairs = None
-        self.capacity = 0
+        self.pool = pairs if pairs is not None else PairPool(self.device)
         self.frame = 0
         self.n_views = 0
         self._keep = None
@@ -95,12 +112,15 @@ class Rasterizer:
         return int(need.value)
 
     def reserve_pairs(self, capacity: int):
-        capacity = int(capacity)
-        need = C.c_size_t()
-        L.check(self.lib.odgs_pair_buffer_size(capacity, C.byref(need)), "odgs_pair_buffer_size")
-        if self.pairs is None or self.pairs.numel() < need.value:
-            self.pairs = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=self.device)
-        self.capacity = capacity
+        self.pool.reserve(self.lib, capacity, self.device)
+
+    @property
+    def capacity(self) -> int:
+        return self.pool.capacity
+
+    @property
+    def pairs(self):
+        return self.pool.tensor
 
     # ---------------------------------------------------------------- passes
     def preprocess(self, means, scales, quats, opacity, sh, views, settings: RenderSettings):

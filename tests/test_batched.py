@@ -97,3 +97,29 @@ def test_autotune_picks_and_caches(tmp_path):
     assert (rs.tile_w, rs.tile_h, rs.batch, rs.pixels_per_thread) in cands
     again = A.autotune(params, sc.views, RenderSettings(sh_degree=1), cache_path=cache, cands=[(8, 8, 32, 2)])
     assert (again.tile_w, again.tile_h) == (rs.tile_w, rs.tile_h)  # served from the cache
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("group", [1, 2])
+def test_grouped_frame_with_recomputed_lists_matches_one_frame(group):
+    import torch
+    from paper_2410_20686_gb300.graph import GroupedFrame, l1_grad
+    from paper_2410_20686_gb300.rasterizer import Rasterizer, RenderSettings
+    sc = _scene()
+    rs = RenderSettings(sh_degree=3)
+    params = [torch.tensor(a, device="cuda") for a in (sc.means, sc.scales, sc.quats, sc.opacity, sc.sh)]
+    targets = [torch.tensor(t, device="cuda") for t in S.target_images(sc, 3)]
+    gfr = GroupedFrame(params, sc.views, targets, rs, group_size=group)
+    gfr.step()
+    torch.cuda.synchronize()
+    assert gfr.status() == 0
+    rast = Rasterizer()
+    imgs, _ = rast.forward(*params, sc.views, rs, want_T=False)
+    _, gi = l1_grad(imgs, targets)
+    ge = rast.backward(gi)
+    for a, b in zip(gfr.images, imgs):
+        assert torch.equal(a, b)
+    for k in NAMES:
+        assert rel_l2(gfr.grads[k].cpu().numpy(), ge[k].cpu().numpy()) < 1e-6, k
+    # the shared pair buffer holds one group's lists, not the frame's
+    assert gfr.pair_buffer_bytes() < rast.pairs.numel()
