@@ -77,7 +77,7 @@ typedef struct {
                            pair buffer last given to odgs_bin_sort, which the caller may
                            reuse for other frames between the forward and backward passes */
     int grad_accumulate;/* 1: gradients are added (+=) to the output arrays; 0: written  */
-    int pixels_per_thread; /* blend kernels: pixels of one row per thread, 1, 2 or 4;
+    int pixels_per_thread; /* blend kernels: pixels of one row per thread, 1, 2, 4 or 8;
                               0 -> the largest that divides tile_w while tile_w * tile_h /
                               pixels_per_thread is a multiple of 32 and at most 256         */
 } odgs_settings;

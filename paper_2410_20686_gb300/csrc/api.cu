@@ -247,7 +247,7 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.dval = reinterpret_cast<uint32_t*>(w + c->L.dval0);
     a.hdr = hdr;
     if (launch_preprocess(a, c->s.sh_degree, st) != cudaSuccess) return ODGS_ERR_CUDA;
-    if (c->n > 0) c->launches += 1;
+    if (c->n > 0) c->launches += 2;
     return ODGS_OK;
 }
 

@@ -1,8 +1,12 @@
 // Per-Gaussian kernels of the ODGS ERP rasterizer (sm_103a):
-//   k_setup          per-view tables (pixel-centre cos/sin in float-float), header reset
-//   k_preprocess     forward projection per (Gaussian, view): Sec. 3.1-3.2, Eq. 4-8
-//   k_preprocess_bwd chain rule from screen-space gradients to the parameters: App. A.3
-// Both per-Gaussian kernels read each Gaussian's parameters once and loop over the views in
+//   k_setup                per-view tables (pixel-centre cos/sin in float-float), header reset
+//   k_preprocess_geom      forward projection per (Gaussian, view): Sec. 3.1-3.2, Eq. 4-8
+//   k_preprocess_color     SH colour per visible (Gaussian, view)
+//   k_preprocess_bwd       chain rule from screen-space gradients to the parameters: App. A.3
+// The forward's geometry and colour halves are separate kernels so that the geometry does not
+// carry the 48 SH coefficients in registers. The backward stays one kernel: split, it would read
+// the screen-space accumulators and the means twice, which measured slower.
+// The per-Gaussian kernels read each Gaussian's parameters once and loop over the views in
 // registers, so a batch of V views costs one parameter read (HBM-bound for SH degree 3).
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
@@ -209,9 +213,7 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int stride
 
 // ------------------------------------------------------------------ forward projection
 
-template <int DEG>
-__global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
+__global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long local_pairs = 0ull;
     if (g < a.n) {
@@ -219,8 +221,6 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
         const float s0 = __ldg(a.scales + 3 * g), s1 = __ldg(a.scales + 3 * g + 1), s2 = __ldg(a.scales + 3 * g + 2);
         const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
         const float o = __ldg(a.opacity + g);
-        float shc[16][3];
-        load_sh<DEG>(a.sh, a.sh_coeffs, g, shc);
 
         // Sigma = M M^T with M = R(q) S (Sec. 3.1)
         float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
@@ -300,23 +300,8 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
                         rect = make_uint4((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count, span[0], span[1]);
                         local_pairs += count;
                         key = __float_as_uint(r);
-                        // view-dependent colour: max(0, sum_k sh_k Y_k(d) + 0.5), d from the
-                        // camera centre to the mean in world space
-                        float dx = m0 - V.cam[0], dy = m1 - V.cam[1], dz = m2 - V.cam[2];
-                        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-                        float Y[16];
-                        sh_basis<DEG>(dx * il, dy * il, dz * il, Y);
-                        float rgb[3];
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            float acc = 0.5f;
-#pragma unroll
-                            for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
-                            rgb[ch] = fmaxf(acc, 0.f);
-                        }
                         a.rec_a[item] = ra;
                         a.rec_b[item] = rb;
-                        a.rec_c[item] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
                     }
                 }
             }
@@ -334,6 +319,38 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
         unsigned long long tot = 0ull;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_sum[w];
         if (tot) atomicAdd(&a.hdr->pairs, tot);
+    }
+}
+
+// View-dependent colour of every visible item: max(0, sum_k sh_k Y_k(d) + 0.5) with d the unit
+// vector from the camera centre to the mean in world space. A separate streaming kernel, so the
+// 48 SH coefficients do not weigh on the geometry kernel's registers.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_preprocess_color(PreArgs a) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
+    bool loaded = false;
+    float shc[16][3];
+    for (int v = 0; v < a.n_views; ++v) {
+        const size_t item = (size_t)v * a.n + g;
+        if (a.dkey[item] == 0xFFFFFFFFu) continue;  // culled in this view
+        if (!loaded) { load_sh<DEG>(a.sh, a.sh_coeffs, g, shc); loaded = true; }
+        const ViewDev& V = a.views[v];
+        const float dx = m0 - V.cam[0], dy = m1 - V.cam[1], dz = m2 - V.cam[2];
+        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis<DEG>(dx * il, dy * il, dz * il, Y);
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
+            rgb[ch] = fmaxf(acc, 0.f);
+        }
+        a.rec_c[item] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
     }
 }
 
@@ -557,12 +574,13 @@ cudaError_t launch_setup(const ViewTable& tab, ViewDev* views, float4* trig, Hea
 
 cudaError_t launch_preprocess(const PreArgs& a, int sh_degree, cudaStream_t st) {
     if (a.n == 0) return cudaSuccess;
-    int threads = 256, blocks = (a.n + threads - 1) / threads;
+    const int threads = 256, blocks = (a.n + threads - 1) / threads;
+    k_preprocess_geom<<<blocks, threads, 0, st>>>(a);
     switch (sh_degree) {
-        case 0: k_preprocess<0><<<blocks, threads, 0, st>>>(a); break;
-        case 1: k_preprocess<1><<<blocks, threads, 0, st>>>(a); break;
-        case 2: k_preprocess<2><<<blocks, threads, 0, st>>>(a); break;
-        default: k_preprocess<3><<<blocks, threads, 0, st>>>(a); break;
+        case 0: k_preprocess_color<0><<<blocks, threads, 0, st>>>(a); break;
+        case 1: k_preprocess_color<1><<<blocks, threads, 0, st>>>(a); break;
+        case 2: k_preprocess_color<2><<<blocks, threads, 0, st>>>(a); break;
+        default: k_preprocess_color<3><<<blocks, threads, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }

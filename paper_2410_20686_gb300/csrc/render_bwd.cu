@@ -258,6 +258,7 @@ int render_bwd_occupancy(int tile_w, int tile_h, int batch, int ppt) {
     int nb = 0;
     cudaError_t e;
     switch (ppt) {
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<8>, threads, sm); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<4>, threads, sm); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<2>, threads, sm); break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<1>, threads, sm); break;
@@ -267,10 +268,11 @@ int render_bwd_occupancy(int tile_w, int tile_h, int batch, int ppt) {
 
 cudaError_t launch_render_bwd(const BwdArgs& a, int grid, cudaStream_t st) {
     const int ppt = a.ppt;
-    if (ppt != 1 && ppt != 2 && ppt != 4) return cudaErrorInvalidValue;
+    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return cudaErrorInvalidValue;
     const int threads = a.tile_w * a.tile_h / ppt;
     const size_t sm = render_bwd_smem(a.batch, threads);
     switch (ppt) {
+        case 8: k_render_bwd<8><<<grid, threads, sm, st>>>(a); break;
         case 4: k_render_bwd<4><<<grid, threads, sm, st>>>(a); break;
         case 2: k_render_bwd<2><<<grid, threads, sm, st>>>(a); break;
         default: k_render_bwd<1><<<grid, threads, sm, st>>>(a); break;

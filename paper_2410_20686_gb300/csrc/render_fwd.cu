@@ -158,7 +158,7 @@ size_t render_fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4) +
 int pixels_per_thread(int tile_w, int tile_h, int want) {
     const int area = tile_w * tile_h;
     auto fits = [&](int p) { return tile_w % p == 0 && (area / p) % 32 == 0 && area / p <= 256; };
-    if (want != 0) return (want == 1 || want == 2 || want == 4) && fits(want) ? want : 0;
+    if (want != 0) return (want == 1 || want == 2 || want == 4 || want == 8) && fits(want) ? want : 0;
     for (int p = 4; p >= 1; p >>= 1)
         if (fits(p)) return p;
     return 0;
@@ -171,6 +171,7 @@ int render_fwd_occupancy(int tile_w, int tile_h, int batch, int ppt) {
     int nb = 0;
     cudaError_t e;
     switch (ppt) {
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<8>, threads, sm); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<4>, threads, sm); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<2>, threads, sm); break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<1>, threads, sm); break;
@@ -180,10 +181,11 @@ int render_fwd_occupancy(int tile_w, int tile_h, int batch, int ppt) {
 
 cudaError_t launch_render_fwd(const FwdArgs& a, int grid, cudaStream_t st) {
     const int ppt = a.ppt;
-    if (ppt != 1 && ppt != 2 && ppt != 4) return cudaErrorInvalidValue;
+    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return cudaErrorInvalidValue;
     const int threads = a.tile_w * a.tile_h / ppt;
     const size_t sm = render_fwd_smem(a.batch);
     switch (ppt) {
+        case 8: k_render_fwd<8><<<grid, threads, sm, st>>>(a); break;
         case 4: k_render_fwd<4><<<grid, threads, sm, st>>>(a); break;
         case 2: k_render_fwd<2><<<grid, threads, sm, st>>>(a); break;
         default: k_render_fwd<1><<<grid, threads, sm, st>>>(a); break;
