@@ -276,14 +276,37 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
     flush_digits(s_hist, a.key_hist, a.key_passes);
 }
 
-__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, const Header* __restrict__ hdr,
-                              uint2* __restrict__ ranges, uint32_t total_tiles) {
+// [start, end) of every tile's run. A thread takes 4 consecutive keys (one 16-byte load when the
+// array is 16-byte aligned) plus the keys on either side.
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const Header* __restrict__ hdr,
+                                                     uint2* __restrict__ ranges, uint32_t total_tiles) {
     const uint32_t n = hdr->n_pairs_sort;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        if (k >= total_tiles) continue;  // only after a failed sort (status already set)
-        if (i == 0u || keys[i - 1] != k) ranges[k].x = i;
-        if (i + 1u == n || keys[i + 1] != k) ranges[k].y = i + 1u;
+    const uint32_t nq = (n + 3u) / 4u;
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0u;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4u * t;
+        uint32_t k[4];
+        if (vec && i0 + 4u <= n) {
+            const uint4 q = *reinterpret_cast<const uint4*>(keys + i0);
+            k[0] = q.x; k[1] = q.y; k[2] = q.z; k[3] = q.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) k[r] = (i0 + (uint32_t)r < n) ? keys[i0 + r] : 0xFFFFFFFFu;
+        }
+        uint32_t prev = i0 > 0u ? keys[i0 - 1u] : 0xFFFFFFFFu;
+        const uint32_t next = (i0 + 4u < n) ? keys[i0 + 4u] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t i = i0 + (uint32_t)r;
+            if (i >= n) break;
+            const uint32_t kk = k[r];
+            const uint32_t kn = r < 3 ? k[r + 1] : next;
+            if (kk < total_tiles) {  // false only after a failed sort (status already set)
+                if (i == 0u || prev != kk) ranges[kk].x = i;
+                if (i + 1u == n || kn != kk) ranges[kk].y = i + 1u;
+            }
+            prev = kk;
+        }
     }
 }
 
@@ -323,7 +346,7 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const Header* hdr, uint2* r
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st);
     if (e != cudaSuccess) return e;
     if (max_pairs == 0) return cudaSuccess;
-    int blocks = (int)min((max_pairs + 255) / 256, (size_t)num_sms * 16);
+    int blocks = (int)min((max_pairs / 4 + 255) / 256, (size_t)num_sms * 16);
     k_tile_ranges<<<max(blocks, 1), 256, 0, st>>>(keys, hdr, ranges, (uint32_t)total_tiles);
     *launches += 1;
     return cudaGetLastError();
