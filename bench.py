@@ -142,6 +142,72 @@ def fp32_peak_tflops(torch, dev, peaks):
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
+# Algorithmic bytes of the HBM-bound stages (each byte the stage must move once):
+#   preprocess     per Gaussian its parameters (means 12, scales 12, quats 16, opacity 4, SH 48 x
+#                  4 at degree 3 = 236 B); per visible item its record (ERP mean 8, conic 12,
+#                  opacity 4, colour 12, depth key 4, tile rectangle 12 = 52 B)
+#   bin_sort       per item: four 8-bit depth-sort passes over key + value (16 B each) and the
+#                  digit counts' read of the keys (4 B); the pair count and the emission read the
+#                  sorted index and the rectangle twice (40 B). Per pair: its key + value written
+#                  (8 B), each tile-sort pass (16 B), the range scan's read of the key (4 B).
+#                  Per tile its range (8 B)
+#   preprocess_bwd per Gaussian its parameters read and their gradients written (2 x 236 B); per
+#                  visible item the 9 accumulated screen-space gradients (36 B)
+def param_bytes(sh_degree):
+    return 4 * (3 + 3 + 4 + 1 + 3 * (sh_degree + 1) ** 2)
+
+
+RECORD_BYTES = 52
+ACC_BYTES = 36
+
+
+def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_tflops, alu_measured):
+    items, vis, pairs = n, stats["visible"], stats["pairs_sorted"]
+    hbm = {
+        "preprocess": n * param_bytes(sh_degree) + vis * RECORD_BYTES,
+        "bin_sort": items * (4 * 16 + 4 + 40) + pairs * (8 + 16 * pair_passes + 4) + tiles * 8,
+        "preprocess_bwd": n * 2 * param_bytes(sh_degree) + vis * ACC_BYTES,
+    }
+    alu = {
+        "render_fwd": FLOP_TESTED * stats["evals_fwd"] + FLOP_BLEND_FWD * stats["blended"],
+        "render_bwd": FLOP_TESTED * stats["evals_bwd"] + FLOP_BLEND_BWD * stats["blended"],
+    }
+    out = {}
+    for k, b in hbm.items():
+        gbs = b / (kern[k] * 1e-3) / 1e9
+        out[k] = {"ms": kern[k], "bound": "hbm", "bytes": b, "achieved": gbs, "unit": "GB/s", "peak": hbm_gbs,
+                  "frac": gbs / hbm_gbs}
+    for k, f in alu.items():
+        tf = f / (kern[k] * 1e-3) / 1e12
+        out[k] = {"ms": kern[k], "bound": "alu", "flops": f, "achieved": tf, "unit": "TFLOP/s", "peak": alu_tflops,
+                  "frac": tf / alu_tflops}
+        if alu_measured:
+            out[k]["frac_of_measured_ffma"] = tf / alu_measured
+    return out
+
+
+# DRAM bytes (read + write) of one k_render_bwd launch on this workload from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid while the kernel's sources hash to the
+# recorded value; after any change the bench reports null until it is captured again.
+PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh", "odgs_internal.h"),
+                    "sha256": "7f308aff108929b8650e6d90782f1a92b04a14cc5660e5e64bf489fc9abbf73f",
+                    "bytes": 170488832}
+
+
+def profiled_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in PROFILED_TRAFFIC["sources"]:
+            with open(os.path.join(ROOT, "paper_2410_20686_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    if PROFILED_TRAFFIC["sha256"] and h.hexdigest() == PROFILED_TRAFFIC["sha256"]:
+        return PROFILED_TRAFFIC["bytes"]
+    return None
+
+
 # ------------------------------------------------------------------ CPU oracle leg
 
 def oracle_sample(scene, n_pix, seed=0):
@@ -181,8 +247,8 @@ def cpu_baseline(scene):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = dist_env()
+    if rank != 0:  # under torchrun only rank 0 times the oracle; the others exit without work
         return
     from paper_2410_20686_gb300 import scenes as S
     from oracle import oracle as O
@@ -269,6 +335,30 @@ def run_batched(dev, rs, steps, warmup):
             "kernel_launches_per_frame": gf.launches, "steps": steps, "per_gpu": True}
 
 
+# ------------------------------------------------------------------ multi-process plumbing
+
+def dist_env():
+    """(world, rank, local_rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x of all ranks (the job's wall time is its slowest rank's)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, seconds_max: float) -> float:
+    """Whole-job iterations per second: every rank ran `steps` independent iterations."""
+    return world * steps / seconds_max
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def run_ours(args):
@@ -280,9 +370,7 @@ def run_ours(args):
     from paper_2410_20686_gb300 import scenes as S
     from paper_2410_20686_gb300.rasterizer import Rasterizer, RenderSettings
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     B.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -341,6 +429,11 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
+    # FP32 FMA and exp2f throughput of this device (own microbenchmark), outside the timed region
+    from paper_2410_20686_gb300.rasterizer import measure_peaks
+    measured = measure_peaks(dev) if rank == 0 else None
+    torch.cuda.synchronize()
+
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -355,11 +448,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    elapsed = start.elapsed_time(stop) / 1e3
-    t = torch.tensor([elapsed], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3, world, dev)
     stats = rast.stats()
     assert stats["status"] == 0, stats
 
@@ -388,11 +477,8 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
-        te = time.perf_counter() - t0
-        tt = torch.tensor([te], device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * K / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+        te = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_rate(world, K, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
 
     if rank != 0:
         if world > 1:
@@ -401,27 +487,33 @@ def run_ours(args):
 
     peaks, peak_src = _peaks()
     peak_tf, sms, mhz = fp32_peak_tflops(torch, dev, peaks)
-    fwd_flops = FLOP_TESTED * stats["evals_fwd"] + FLOP_BLEND_FWD * stats["blended"]
-    bwd_flops = FLOP_TESTED * stats["evals_bwd"] + FLOP_BLEND_BWD * stats["blended"]
+    tiles = (view.width // tw) * ((view.height + th - 1) // th)
+    pair_passes = (max(1, (tiles - 1).bit_length()) + 7) // 8  # 8-bit passes over the tile id
+    kernels = stage_rooflines(kern, stats, args.n, 3, tiles, pair_passes, float(peaks["hbm_gbs"]), peak_tf,
+                              measured["ffma_tflops"] if measured else None)
     dom = max(("render_fwd", "render_bwd"), key=lambda k: kern[k])
-    dom_flops = fwd_flops if dom == "render_fwd" else bwd_flops
-    achieved = dom_flops / (kern[dom] * 1e-3) / 1e12
+    d = kernels[dom]
     roofline = {"bound": "alu", "kernel": "k_render_fwd" if dom == "render_fwd" else "k_render_bwd",
-                "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
-                "traffic": None,
+                "achieved": d["achieved"], "peak": peak_tf, "unit": "TFLOP/s", "frac": d["frac"],
+                "traffic": profiled_traffic() if dom == "render_bwd" else None,
                 "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (max SM clock, "
                              f"{peak_src} peaks file)",
                 "units": {"evals_fwd": stats["evals_fwd"], "evals_bwd": stats["evals_bwd"],
-                          "blended": stats["blended"], "pairs": stats["pairs"]}}
+                          "blended": stats["blended"], "pairs": stats["pairs"],
+                          "entries_tile": stats["entries_tile"], "visible": stats["visible"]}}
+    if measured:
+        roofline["peak_measured"] = measured
+        roofline["frac_of_measured_ffma"] = d.get("frac_of_measured_ffma")
 
-    out = {"metric": METRIC, "value": world * K / elapsed, "unit": UNIT, "n_gpus": world, "steps": K,
+    out = {"metric": METRIC, "value": job_rate(world, K, elapsed), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2,
                       "sh_degree": 3, "tile": args.tile, "batch": args.batch, "pixels_per_thread": args.ppt,
                       "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
                       "parallelism": f"replicas x{world}"},
-           "roofline": roofline, "kernels_ms": kern, "gpu_launches": launches_per_step * K, "clocks": clocks}
+           "roofline": roofline, "kernels_ms": kern, "kernels": kernels, "gpu_launches": launches_per_step * K,
+           "clocks": clocks}
     if e2e:
         out["e2e"] = e2e
     if not args.no_batched:

@@ -151,6 +151,10 @@ typedef struct {
     uint64_t evals_fwd;     /* (pixel, list entry) evaluations of the last odgs_render_fwd    */
     uint64_t evals_bwd;     /* (pixel, list entry) evaluations of the last odgs_render_bwd    */
     uint64_t blended;       /* (pixel, Gaussian) pairs blended by the last odgs_render_fwd    */
+    uint64_t entries_tile;  /* sum over tiles of the list entries the last odgs_render_fwd
+                               processed until every pixel of the tile had stopped (each pixel
+                               itself stops earlier: evals_fwd counts only its own entries)   */
+    uint64_t visible;       /* (view, Gaussian) items that survived culling in odgs_preprocess */
     uint32_t status;        /* device status bits (ODGS_DEV_*)                                */
 } odgs_stats;
 
@@ -177,6 +181,19 @@ odgs_status odgs_get_status(odgs_ctx *ctx, uint32_t *bits, void *stream);
  * overlaps on the GPU (other streams, unordered host threads) race on it. */
 odgs_status odgs_render_fwd_static(const odgs_gaussians *g, const odgs_view *view, const odgs_settings *s,
                                    float *image, float *final_T, uint32_t *status_out, void *stream);
+
+/* Throughput of the arithmetic that bounds the blend kernels, measured on the current device
+ * with CUDA events over every SM: independent FP32 FMA chains (an FMA counts 2 flop) and chains
+ * of exp2f, the exponential the blend evaluates. They are the denominators of the blend
+ * kernels' rooflines. Synchronizes the stream; allocates and frees one device buffer of
+ * (SMs * 1024) floats; takes a few tens of milliseconds. */
+typedef struct {
+    double ffma_tflops; /* FP32 FMA throughput, TFLOP/s                               */
+    double ex2_gops;    /* exp2f results per second, in units of 1e9                  */
+    int sms;            /* multiprocessors of the device (all of them are used)       */
+} odgs_peaks;
+
+odgs_status odgs_measure_peaks(odgs_peaks *out, void *stream);
 
 /* Kernel launches the last frame issued (for accounting). */
 int odgs_last_launch_count(const odgs_ctx *ctx);

@@ -21,7 +21,7 @@ MAX_VIEWS = 64
 EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buffer_size",
             "odgs_preprocess", "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd",
             "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
-            "odgs_render_fwd_static", "odgs_last_launch_count", "odgs_status_string")
+            "odgs_render_fwd_static", "odgs_measure_peaks", "odgs_last_launch_count", "odgs_status_string")
 
 
 class OdgsError(RuntimeError):
@@ -48,7 +48,12 @@ class Gaussians(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("pairs_sorted", C.c_uint64), ("evals_fwd", C.c_uint64),
-                ("evals_bwd", C.c_uint64), ("blended", C.c_uint64), ("status", C.c_uint32)]
+                ("evals_bwd", C.c_uint64), ("blended", C.c_uint64), ("entries_tile", C.c_uint64),
+                ("visible", C.c_uint64), ("status", C.c_uint32)]
+
+
+class Peaks(C.Structure):
+    _fields_ = [("ffma_tflops", C.c_double), ("ex2_gops", C.c_double), ("sms", C.c_int)]
 
 
 class Grads(C.Structure):
@@ -84,13 +89,15 @@ def load(path: str = LIB_PATH):
     L.odgs_frame_stats.argtypes = [vp, C.POINTER(Stats), vp]
     L.odgs_get_status.argtypes = [vp, C.POINTER(C.c_uint32), vp]
     L.odgs_render_fwd_static.argtypes = [C.POINTER(Gaussians), C.POINTER(View), C.POINTER(Settings), vp, vp, vp, vp]
+    L.odgs_measure_peaks.argtypes = [C.POINTER(Peaks), vp]
     L.odgs_last_launch_count.argtypes = [vp]
     L.odgs_last_launch_count.restype = C.c_int
     L.odgs_status_string.argtypes = [C.c_int]
     L.odgs_status_string.restype = C.c_char_p
     for name in ("odgs_create", "odgs_workspace_size", "odgs_pair_buffer_size", "odgs_preprocess",
                  "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
-                 "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static"):
+                 "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static",
+                 "odgs_measure_peaks"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -416,8 +416,7 @@ odgs_status odgs_render_fwd(odgs_ctx* c, float* const* images, float* const* fin
     for (int i = 0; i < 3; ++i) a.bg[i] = c->s.bg[i];
     a.hdr = hdr;
     if (cudaMemsetAsync(&hdr->work_fwd, 0, sizeof(uint32_t), st) != cudaSuccess) return ODGS_ERR_CUDA;
-    if (cudaMemsetAsync(&hdr->evals_fwd, 0, sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
-    if (cudaMemsetAsync(&hdr->blended, 0, sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
+    if (cudaMemsetAsync(&hdr->evals_fwd, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
     const int grid = persistent_grid(c, render_fwd_occupancy(c->s.tile_w, c->s.tile_h, a.batch, a.ppt));
     if (launch_render_fwd(a, grid, st) != cudaSuccess) return ODGS_ERR_CUDA;
     c->launches += 1;
@@ -505,6 +504,8 @@ odgs_status odgs_frame_stats(odgs_ctx* c, odgs_stats* out, void* stream) {
     out->evals_fwd = h.evals_fwd;
     out->evals_bwd = h.evals_bwd;
     out->blended = h.blended;
+    out->entries_tile = h.entries_tile;
+    out->visible = h.visible;
     out->status = h.status;
     return ODGS_OK;
 }

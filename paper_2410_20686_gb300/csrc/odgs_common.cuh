@@ -45,9 +45,13 @@ struct ViewDev {
 struct Header {
     unsigned long long pairs;         // total (tile, Gaussian) pairs counted by the preprocess
     unsigned long long pairs_emitted; // min(pairs, capacity) used by the tile sort
-    unsigned long long evals_fwd;     // (pixel, entry) evaluations of the last forward blend
+    unsigned long long visible;       // (view, Gaussian) items that survived culling
     unsigned long long evals_bwd;     // (pixel, entry) evaluations of the last backward blend
+    // forward counters, contiguous so that one memset clears them
+    unsigned long long evals_fwd;     // (pixel, entry) evaluations of the last forward blend
     unsigned long long blended;       // (pixel, entry) pairs blended by the last forward pass
+    unsigned long long entries_tile;  // sum over tiles of the entries processed until all the
+                                      // tile's pixels had stopped
     uint32_t status;
     uint32_t n_items;                 // views * n
     uint32_t n_pairs_sort;            // 32-bit copy of pairs_emitted for the sort kernels

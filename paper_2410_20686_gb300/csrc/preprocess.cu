@@ -24,6 +24,8 @@ __global__ void k_setup(ViewTable tab, ViewDev* views, float4* trig, Header* hdr
         hdr->evals_fwd = 0ull;
         hdr->evals_bwd = 0ull;
         hdr->blended = 0ull;
+        hdr->entries_tile = 0ull;
+        hdr->visible = 0ull;
         hdr->status = 0u;
         hdr->n_items = tab.n_items;
         hdr->n_pairs_sort = 0u;
@@ -216,6 +218,7 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int stride
 __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long local_pairs = 0ull;
+    uint32_t local_visible = 0u;
     if (g < a.n) {
         const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
         const float s0 = __ldg(a.scales + 3 * g), s1 = __ldg(a.scales + 3 * g + 1), s2 = __ldg(a.scales + 3 * g + 2);
@@ -299,6 +302,7 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                     if (count > 0u) {
                         rect = make_uint4((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count, span[0], span[1]);
                         local_pairs += count;
+                        ++local_visible;
                         key = __float_as_uint(r);
                         a.rec_a[item] = ra;
                         a.rec_b[item] = rb;
@@ -310,15 +314,26 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
             a.dval[item] = (uint32_t)item;
         }
     }
-    // frame pair count
-    for (int off = 16; off > 0; off >>= 1) local_pairs += __shfl_xor_sync(0xffffffffu, local_pairs, off);
+    // frame pair and visible-item counts
+    for (int off = 16; off > 0; off >>= 1) {
+        local_pairs += __shfl_xor_sync(0xffffffffu, local_pairs, off);
+        local_visible += __shfl_xor_sync(0xffffffffu, local_visible, off);
+    }
     __shared__ unsigned long long s_sum[8];
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = local_pairs;
+    __shared__ uint32_t s_vis[8];
+    if ((threadIdx.x & 31) == 0) {
+        s_sum[threadIdx.x >> 5] = local_pairs;
+        s_vis[threadIdx.x >> 5] = local_visible;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long tot = 0ull;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_sum[w];
+        unsigned long long tot = 0ull, vis = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            tot += s_sum[w];
+            vis += s_vis[w];
+        }
         if (tot) atomicAdd(&a.hdr->pairs, tot);
+        if (vis) atomicAdd(&a.hdr->visible, vis);
     }
 }
 

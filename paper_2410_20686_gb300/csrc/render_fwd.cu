@@ -30,16 +30,23 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
     float4* s_col = smem + 2 * B;
     float* s_fc2 = reinterpret_cast<float*>(smem + 3 * B);
     __shared__ int s_item;
+    __shared__ uint32_t s_etile;  // entries the current tile processed until its pixels stopped
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int tw = a.tile_w;
     const int tpr = tw / PPT;  // threads per pixel row
     const int lx0 = (tid % tpr) * PPT, ly = tid / tpr;
     uint32_t evals = 0u, blended = 0u;  // (pixel, entry) evaluations / blends by this thread
+    unsigned long long etile = 0ull;    // thread 0: sum of s_etile over this CTA's tiles
+    if (tid == 0) s_etile = 0u;
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = (int)atomicAdd(&a.hdr->work_fwd, 1u);
+        if (tid == 0) {
+            etile += s_etile;
+            s_etile = 0u;
+            s_item = (int)atomicAdd(&a.hdr->work_fwd, 1u);
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= a.total_tiles) break;
@@ -129,6 +136,11 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
             }
             if (__syncthreads_count(alive > 0) == 0) break;
         }
+        int tmax = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) tmax = max(tmax, tested[k]);
+        tmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)tmax);
+        if ((tid & 31) == 0 && tmax > 0) atomicMax(&s_etile, (uint32_t)tmax);
         if (inside) {
             const int HW = V.W * V.H;
             float* img = a.images[v];
@@ -151,6 +163,7 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
     unsigned long long bl = blended;
     for (int o = 16; o > 0; o >>= 1) bl += __shfl_xor_sync(0xffffffffu, bl, o);
     if ((tid & 31) == 0 && bl) atomicAdd(&a.hdr->blended, bl);
+    if (tid == 0 && etile) atomicAdd(&a.hdr->entries_tile, etile);
 }
 
 size_t render_fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4) + sizeof(float)); }

@@ -205,7 +205,8 @@ class Rasterizer:
         stream = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
         L.check(self.lib.odgs_frame_stats(self.ctx, C.byref(s), stream), "odgs_frame_stats")
         return dict(pairs=int(s.pairs), pairs_sorted=int(s.pairs_sorted), evals_fwd=int(s.evals_fwd),
-                    evals_bwd=int(s.evals_bwd), blended=int(s.blended), status=int(s.status))
+                    evals_bwd=int(s.evals_bwd), blended=int(s.blended), entries_tile=int(s.entries_tile),
+                    visible=int(s.visible), status=int(s.status))
 
     def status(self) -> int:
         bits = C.c_uint32()
@@ -255,3 +256,14 @@ def render(means, scales, quats, opacity, sh, views, settings: RenderSettings = 
     settings = settings or RenderSettings()
     rast = rasterizer or Rasterizer(means.device)
     return ODGSRender.apply(rast, settings, list(views), means, scales, quats, opacity, sh)
+
+
+def measure_peaks(device=None) -> dict:
+    """FP32 FMA (TFLOP/s) and exp2f (G/s) throughput of the current device, by odgs_measure_peaks."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    lib = L.load()
+    p = L.Peaks()
+    with torch.cuda.device(dev):
+        stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        L.check(lib.odgs_measure_peaks(C.byref(p), stream), "odgs_measure_peaks")
+    return {"ffma_tflops": float(p.ffma_tflops), "ex2_gops": float(p.ex2_gops), "sms": int(p.sms)}
