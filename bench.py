@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the blend kernels (0 = auto)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view batched measurement")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--no-next", action="store_true", help="skip the measurements of the steps after the hot path")
     return ap.parse_args()
 
 
@@ -335,6 +336,63 @@ def run_batched(dev, rs, steps, warmup):
             "kernel_launches_per_frame": gf.launches, "steps": steps, "per_gpu": True}
 
 
+# ------------------------------------------------------------------ densification (Sec. 3.3)
+
+def timed_flushed(torch, dev, fn, iters):
+    """Mean CUDA-event milliseconds of fn over iters calls, each after an L2 flush (a 256 MB write)."""
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    total = 0.0
+    for _ in range(iters):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        total += e0.elapsed_time(e1)
+    return total / iters
+
+
+def run_densify(torch, dev, rast, params, view, rs, target, hbm_gbs, iters=20):
+    """Statistics over a few frames, then the decision and the densified arrays, timed."""
+    from paper_2410_20686_gb300.densify import DensifyParams, DensifyStats, apply, select
+    n = params[0].shape[0]
+    stats = DensifyStats(n, dev)
+    grads = {k: torch.empty_like(t) for k, t in zip(("means", "scales", "quats", "opacity", "sh"), params)}
+    for _ in range(4):
+        imgs, _ = rast.forward(*params, [view], rs, want_T=False)
+        g = torch.sign(imgs[0] - target) * (1.0 / imgs[0].numel())
+        rast.render_bwd([g])
+        rast.preprocess_bwd(grads, densify=stats)
+    # the fused statistics' cost: the backward preprocess with and without them
+    t_plain = timed_flushed(torch, dev, lambda: rast.preprocess_bwd(grads), iters)
+    t_stats = timed_flushed(torch, dev, lambda: rast.preprocess_bwd(grads, densify=stats), iters)
+    prm = DensifyParams(scene_extent=10.0)
+    act = select(stats, params[1], params[3], prm)
+    t_sel = timed_flushed(torch, dev, lambda: select(stats, params[1], params[3], prm), iters)
+    noise = torch.randn((n, 2, 3), device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    out = apply(*params, act, noise)
+    t_app = timed_flushed(torch, dev, lambda: apply(*params, act, noise), max(3, iters // 4))
+    a = act.cpu()
+    kept, clone, split = int(((a == 0) | (a == 1)).sum()), int((a == 1).sum()), int((a == 2).sum())
+    pbytes = param_bytes(3)
+    # select: statistics 12 B, scales 12 B, opacity 4 B read, one action byte written
+    sel_bytes = n * (12 + 12 + 4 + 1)
+    # apply: actions read twice (count and scatter), each used Gaussian's parameters read once, the
+    # noise of split ones, every output written
+    used = kept + split
+    app_bytes = 2 * n + used * pbytes + split * 24 + out[0].shape[0] * pbytes
+    return {"workload": "statistics of 4 fwd+bwd frames of the 1M-Gaussian view, then one densification "
+                        "(tau_min 2e-5, tau_max 1e-4, percent_dense 1e-3, scene extent 10)",
+            "stats_overhead_ms": t_stats - t_plain, "preprocess_bwd_ms": t_plain,
+            "select_ms": t_sel, "select_gbs": sel_bytes / (t_sel * 1e-3) / 1e9,
+            "select_frac": sel_bytes / (t_sel * 1e-3) / 1e9 / hbm_gbs,
+            "apply_ms": t_app, "apply_gbs": app_bytes / (t_app * 1e-3) / 1e9,
+            "apply_frac": app_bytes / (t_app * 1e-3) / 1e9 / hbm_gbs,
+            "kept": kept, "cloned": clone, "split": split, "pruned": n - kept - split, "n_out": int(out[0].shape[0]),
+            "l2": "flushed before every timed call"}
+
+
 # ------------------------------------------------------------------ multi-process plumbing
 
 def dist_env():
@@ -518,6 +576,8 @@ def run_ours(args):
         out["e2e"] = e2e
     if not args.no_batched:
         out["batched"] = run_batched(dev, rs, args.batched_steps, args.warmup)
+    if not args.no_next:
+        out["next"] = {"densify": run_densify(torch, dev, rast, params, view, rs, target, float(peaks["hbm_gbs"]))}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(out), flush=True)

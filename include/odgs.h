@@ -91,9 +91,19 @@ typedef struct {
     int n;
 } odgs_gaussians;
 
-/* Parameter gradients, device pointers with the layouts of odgs_gaussians. */
+/* Parameter gradients, device pointers with the layouts of odgs_gaussians.
+ * Optional densification statistics (Sec. 3.3): three device arrays of n elements, all given or
+ * all NULL. odgs_preprocess_bwd always ADDS to them (they run over many frames until the caller
+ * densifies and clears them): for every view in which the Gaussian survived culling,
+ *   densify_grad  += || (dL/du * W/2, dL/dv * H/2) ||   (the frame's ERP-mean gradient in the
+ *                                                       [-1, 1] image coordinates of 3DGS)
+ *   densify_elev  += 1 - cos(theta)                      (theta: elevation of the mean, Eq. 4)
+ *   densify_count += 1
+ * odgs_densify_select (odgs_train.h) turns them into clone / split / prune decisions. */
 typedef struct {
     float *means, *scales, *quats, *opacity, *sh;
+    float *densify_grad, *densify_elev;
+    uint32_t *densify_count;
 } odgs_grads;
 
 typedef struct odgs_ctx odgs_ctx;

@@ -1,0 +1,77 @@
+/*
+ * odgs_train.h -- C ABI of the training-side steps around the ODGS rasterizer (sm_103a).
+ *
+ * Densification (ODGS Sec. 3.3, hyper-parameters of App. A.1). ODGS keeps the densification
+ * loop of 3D Gaussian splatting and makes its gradient threshold depend on the elevation of the
+ * Gaussian seen from the camera,
+ *     tau_mu = tau_min + (1 - cos theta_mu) (tau_max - tau_min),   tau_min = 2e-5, tau_max = 1e-4,
+ * because the ERP projection stretches Gaussians near the poles. The statistics are gathered by
+ * odgs_preprocess_bwd (odgs_grads.densify_*, odgs.h); the calls below turn them into decisions
+ * and build the densified parameter arrays.
+ *
+ * All pointers are device pointers owned by the caller unless noted; the structs are host
+ * memory read during the call. Calls are asynchronous on the given stream (cudaStream_t as
+ * void*, NULL = legacy default stream) and allocate nothing.
+ */
+#ifndef ODGS_TRAIN_H
+#define ODGS_TRAIN_H
+
+#include "odgs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Densification actions (one byte per Gaussian). */
+#define ODGS_KEEP 0u
+#define ODGS_CLONE 1u /* kept, plus one identical copy                                    */
+#define ODGS_SPLIT 2u /* replaced by two children at mu + R(q)(s * z), scales s / 1.6       */
+#define ODGS_PRUNE 4u /* removed                                                           */
+
+typedef struct {
+    float tau_min, tau_max; /* thresholds at the equator and at the poles (2e-5, 1e-4)          */
+    float percent_dense;    /* clone when max scale <= percent_dense * scene_extent, else split
+                               (App. A.1: 1e-3)                                                  */
+    float scene_extent;     /* > 0                                                               */
+    float min_opacity;      /* prune when opacity < min_opacity (3DGS: 0.005)                    */
+    float max_scale;        /* prune when a scale > max_scale; 0 disables                        */
+} odgs_densify_params;
+
+/* Decision per Gaussian from the accumulated statistics (float32 arithmetic, fixed order):
+ *   c = count[i]; if c > 0: g = grad[i] / c, e = elev[i] / c (each one IEEE division)
+ *   tau = tau_min + e * (tau_max - tau_min)   (one rounded product, one rounded sum)
+ *   densify = c > 0 && g >= tau;  big = max(scales[i]) > percent_dense * scene_extent
+ *   action = prune ? ODGS_PRUNE : densify ? (big ? ODGS_SPLIT : ODGS_CLONE) : ODGS_KEEP
+ * grad, elev: [n] float; count: [n] uint32; scales [n][3] and opacity [n] activated; action: [n]
+ * bytes written. n >= 0. */
+odgs_status odgs_densify_select(const float *grad, const float *elev, const uint32_t *count,
+                                const float *scales, const float *opacity, int n,
+                                const odgs_densify_params *p, uint8_t *action, void *stream);
+
+/* Output parameter arrays (device, layouts of odgs_gaussians). */
+typedef struct {
+    float *means, *scales, *quats, *opacity, *sh;
+} odgs_params_out;
+
+/* Bytes of scratch odgs_densify_apply needs for n Gaussians (host-only, pure). */
+odgs_status odgs_densify_scratch_size(int n, size_t *bytes);
+
+/* Builds the densified Gaussians from in (n Gaussians, sh_coeffs coefficients each) and action:
+ *   [0, K)                 Gaussians with ODGS_KEEP or ODGS_CLONE, in index order
+ *   [K, K + C)             the copies of the ODGS_CLONE ones, in index order
+ *   [K + C, K + C + S)     the first children of the ODGS_SPLIT ones, in index order
+ *   [K + C + S, K + C + 2S) their second children
+ * A child c of Gaussian i sits at mu_i + R(q_i) (s_i * noise[i][c]) (noise: [n][2][3] standard
+ * normal draws, read for split Gaussians only) with scales s_i / 1.6; rotation, opacity and SH
+ * are copied. *n_out (device, one uint32) receives K + C + 2S; outputs at or beyond out_capacity
+ * are not written (the caller compares *n_out with its capacity). The output arrays must not
+ * overlap the inputs. scratch: odgs_densify_scratch_size(n) bytes, 16-byte aligned. */
+odgs_status odgs_densify_apply(const odgs_gaussians *in, int sh_coeffs, const uint8_t *action,
+                               const float *noise, const odgs_params_out *out, int out_capacity,
+                               uint32_t *n_out, void *scratch, size_t scratch_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ODGS_TRAIN_H */

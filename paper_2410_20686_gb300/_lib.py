@@ -11,6 +11,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libodgs.so")
 
 ODGS_OK = 0
+ODGS_ERR_INVALID_ARG, ODGS_ERR_CAPACITY, ODGS_ERR_CUDA, ODGS_ERR_TIMEOUT = -1, -2, -3, -4
+ODGS_ERR_STATE, ODGS_ERR_WORKSPACE = -6, -7
 STATUS_NAMES = {0: "ODGS_OK", -1: "ODGS_ERR_INVALID_ARG", -2: "ODGS_ERR_CAPACITY", -3: "ODGS_ERR_CUDA",
                 -4: "ODGS_ERR_TIMEOUT", -6: "ODGS_ERR_STATE", -7: "ODGS_ERR_WORKSPACE"}
 DEV_CAPACITY = 1
@@ -21,7 +23,8 @@ MAX_VIEWS = 64
 EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buffer_size",
             "odgs_preprocess", "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd",
             "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
-            "odgs_render_fwd_static", "odgs_measure_peaks", "odgs_last_launch_count", "odgs_status_string")
+            "odgs_render_fwd_static", "odgs_measure_peaks", "odgs_last_launch_count", "odgs_status_string",
+            "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply")
 
 
 class OdgsError(RuntimeError):
@@ -52,13 +55,24 @@ class Stats(C.Structure):
                 ("visible", C.c_uint64), ("status", C.c_uint32)]
 
 
+class DensifyParams(C.Structure):
+    _fields_ = [("tau_min", C.c_float), ("tau_max", C.c_float), ("percent_dense", C.c_float),
+                ("scene_extent", C.c_float), ("min_opacity", C.c_float), ("max_scale", C.c_float)]
+
+
+class ParamsOut(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+
+
 class Peaks(C.Structure):
     _fields_ = [("ffma_tflops", C.c_double), ("ex2_gops", C.c_double), ("sms", C.c_int)]
 
 
 class Grads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
-                ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+                ("opacity", C.c_void_p), ("sh", C.c_void_p), ("densify_grad", C.c_void_p),
+                ("densify_elev", C.c_void_p), ("densify_count", C.c_void_p)]
 
 
 _lib = None
@@ -90,6 +104,10 @@ def load(path: str = LIB_PATH):
     L.odgs_get_status.argtypes = [vp, C.POINTER(C.c_uint32), vp]
     L.odgs_render_fwd_static.argtypes = [C.POINTER(Gaussians), C.POINTER(View), C.POINTER(Settings), vp, vp, vp, vp]
     L.odgs_measure_peaks.argtypes = [C.POINTER(Peaks), vp]
+    L.odgs_densify_select.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.POINTER(DensifyParams), vp, vp]
+    L.odgs_densify_scratch_size.argtypes = [C.c_int, C.POINTER(sz)]
+    L.odgs_densify_apply.argtypes = [C.POINTER(Gaussians), C.c_int, vp, vp, C.POINTER(ParamsOut), C.c_int, vp, vp,
+                                     sz, vp]
     L.odgs_last_launch_count.argtypes = [vp]
     L.odgs_last_launch_count.restype = C.c_int
     L.odgs_status_string.argtypes = [C.c_int]
@@ -97,7 +115,7 @@ def load(path: str = LIB_PATH):
     for name in ("odgs_create", "odgs_workspace_size", "odgs_pair_buffer_size", "odgs_preprocess",
                  "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
                  "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static",
-                 "odgs_measure_peaks"):
+                 "odgs_measure_peaks", "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -475,9 +475,18 @@ odgs_status odgs_preprocess_bwd(odgs_ctx* c, const odgs_grads* grads, void* stre
     if (c->n > 0 && reinterpret_cast<uintptr_t>(grads->quats) % 16 != 0) return ODGS_ERR_INVALID_ARG;
     if (c->n > 0 && (c->s.sh_coeffs * 3) % 4 == 0 && reinterpret_cast<uintptr_t>(grads->sh) % 16 != 0)
         return ODGS_ERR_INVALID_ARG;
+    const int dens = (grads->densify_grad != nullptr) + (grads->densify_elev != nullptr) +
+                     (grads->densify_count != nullptr);
+    if (dens != 0 && dens != 3) return ODGS_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint8_t* w = c->ws;
     PreBwdArgs b{};
+    b.rect = reinterpret_cast<const uint4*>(w + c->L.rect);
+    if (dens == 3) {
+        b.d_grad = grads->densify_grad;
+        b.d_elev = grads->densify_elev;
+        b.d_count = grads->densify_count;
+    }
     b.means = c->g.means; b.scales = c->g.scales; b.quats = c->g.quats; b.opacity = c->g.opacity; b.sh = c->g.sh;
     b.n = c->n; b.n_views = c->V; b.sh_coeffs = c->s.sh_coeffs;
     b.views = reinterpret_cast<const ViewDev*>(w + c->L.views);

@@ -123,6 +123,13 @@ struct Staged {
     float fc2;   // column anchor right of the seam split
 };
 
+// Rotation matrix of the normalized quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
 // Seam shift for pixel column i: the image of the Gaussian nearest to the pixel, so that the
 // horizontal offset lies in [-W/2, W/2).
 __device__ __forceinline__ int seam_shift(int i, int c0, float du, int W) {

@@ -35,6 +35,9 @@ struct PreBwdArgs {
     const float4* acc;
     float *g_means, *g_scales, *g_quats, *g_opacity, *g_sh;
     int accumulate;
+    const uint4* rect;               // footprint words: tile count > 0 <=> visible in that view
+    float *d_grad, *d_elev;          // densification statistics (all three or none)
+    uint32_t* d_count;
 };
 
 struct BinArgs {

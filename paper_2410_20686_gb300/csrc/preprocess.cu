@@ -54,12 +54,6 @@ __global__ void k_setup(ViewTable tab, ViewDev* views, float4* trig, Header* hdr
 
 // ------------------------------------------------------------------ shared math
 
-// Rotation matrix of the normalized quaternion (w, x, y, z).
-__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
-    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
-    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
-    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
-}
 
 // Real SH basis (orthonormal, no Condon-Shortley phase) as Cartesian polynomials of the unit
 // direction (x, y, z); index l^2 + l + m.
@@ -400,9 +394,33 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
     bool any = false;
     bool sh_loaded = false;
     float shc[16][3];
+    // densification statistics of this Gaussian (Sec. 3.3): the running sums are loaded here, so
+    // their latency overlaps the loop instead of ending every thread
+    float st_grad = 0.f, st_elev = 0.f;
+    uint32_t st_count = 0u;
+    if (a.d_count) {
+        st_grad = a.d_grad[g];
+        st_elev = a.d_elev[g];
+        st_count = a.d_count[g];
+    }
+    const uint32_t st_count0 = st_count;
     for (int v = 0; v < a.n_views; ++v) {
         const size_t item = (size_t)v * a.n + g;
         const float4 g0 = a.acc[3 * item], g1 = a.acc[3 * item + 1], g2 = a.acc[3 * item + 2];
+        if (a.d_count && a.rect[item].y > 0u) {
+            // visible in view v: ERP-mean gradient in [-1, 1] image units, and 1 - cos(theta)
+            // as t_y^2 / (r (r + rho)), free of the cancellation of 1 - rho / r
+            const ViewDev& V = a.views[v];
+            float t[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) t[i] = V.R[3 * i] * m0 + V.R[3 * i + 1] * m1 + V.R[3 * i + 2] * m2 + V.t[i];
+            const float rho = sqrtf(t[0] * t[0] + t[2] * t[2]);
+            const float r = sqrtf(rho * rho + t[1] * t[1]);
+            const float gu = g0.x * (0.5f * (float)V.W), gv = g0.y * (0.5f * (float)V.H);
+            st_grad += sqrtf(gu * gu + gv * gv);
+            st_elev += t[1] * t[1] / (r * (r + rho));
+            ++st_count;
+        }
         // accumulator layout: (du, dv, da, db), (dc, dopacity, dr, dg), (db, 0, 0, 0)
         if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
             g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
@@ -511,6 +529,12 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
             gm[1] += (gy - dd * y) * il;
             gm[2] += (gz - dd * z) * il;
         }
+    }
+
+    if (a.d_count && st_count != st_count0) {  // this thread owns Gaussian g
+        a.d_grad[g] = st_grad;
+        a.d_elev[g] = st_elev;
+        a.d_count[g] = st_count;
     }
 
     float gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};

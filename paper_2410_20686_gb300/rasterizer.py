@@ -184,21 +184,31 @@ class Rasterizer:
         L.check(self.lib.odgs_render_bwd(self.ctx, arr, stream), "odgs_render_bwd")
         self._gi_keep = gi
 
-    def preprocess_bwd(self, grads=None):
-        """Chain rule to the five parameter gradients (written, or added when grad_accumulate)."""
+    def preprocess_bwd(self, grads=None, densify=None):
+        """Chain rule to the five parameter gradients (written, or added when grad_accumulate).
+        densify: optional object with float32 ``grad``, ``elev`` and int32 ``count`` tensors [n]
+        to which the frame's densification statistics are added (Sec. 3.3)."""
         means, scales, quats, opacity, sh = self._keep
         if grads is None:
             grads = dict(means=torch.empty_like(means), scales=torch.empty_like(scales),
                          quats=torch.empty_like(quats), opacity=torch.empty_like(opacity), sh=torch.empty_like(sh))
         gc = L.Grads(_ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]), _ptr(grads["opacity"]),
                      _ptr(grads["sh"]))
+        if densify is not None:
+            n = means.shape[0]
+            for name, dt in (("grad", torch.float32), ("elev", torch.float32), ("count", torch.int32)):
+                t = getattr(densify, name)
+                if t.dtype != dt or t.numel() != n or not t.is_contiguous() or t.device != means.device:
+                    raise ValueError(f"densify.{name} must be a contiguous {dt} tensor of {n} elements on {means.device}")
+            gc.densify_grad, gc.densify_elev, gc.densify_count = (_ptr(densify.grad), _ptr(densify.elev),
+                                                                  _ptr(densify.count))
         stream = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
         L.check(self.lib.odgs_preprocess_bwd(self.ctx, C.byref(gc), stream), "odgs_preprocess_bwd")
         return grads
 
-    def backward(self, grad_images, grads=None):
+    def backward(self, grad_images, grads=None, densify=None):
         self.render_bwd(grad_images)
-        return self.preprocess_bwd(grads)
+        return self.preprocess_bwd(grads, densify)
 
     def stats(self) -> dict:
         s = L.Stats()

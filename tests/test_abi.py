@@ -19,7 +19,8 @@ def lib():
 
 
 def _declared_functions():
-    text = open(os.path.join(ROOT, "include", "odgs.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(odgs_[a-z_0-9]+)\s*\(", text)))
 
