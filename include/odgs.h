@@ -80,6 +80,10 @@ typedef struct {
     int pixels_per_thread; /* blend kernels: pixels of one row per thread, 1, 2, 4 or 8;
                               0 -> the largest that divides tile_w while tile_w * tile_h /
                               pixels_per_thread is a multiple of 32 and at most 256         */
+    int raw_params;     /* 1: odgs_gaussians.scales hold log-scales and .opacity logits, the
+                           variables 3DGS optimises; the library applies exp and the sigmoid
+                           and odgs_preprocess_bwd returns the gradients w.r.t. these raw
+                           variables. 0: activated values (scales > 0, opacity in (0, 1)) */
 } odgs_settings;
 
 /* Gaussian parameters, device pointers, float32, contiguous:

@@ -35,15 +35,21 @@ typedef struct {
     float scene_extent;     /* > 0                                                               */
     float min_opacity;      /* prune when opacity < min_opacity (3DGS: 0.005)                    */
     float max_scale;        /* prune when a scale > max_scale; 0 disables                        */
+    int raw_params;         /* 1: scales are log-scales and opacity logits (odgs_settings
+                               .raw_params); the comparisons below then run in that space, against
+                               thresholds computed once on the host in double precision and
+                               rounded to float: log(percent_dense * scene_extent), the logit of
+                               min_opacity, log(max_scale); split children get log s - log 1.6 */
 } odgs_densify_params;
 
 /* Decision per Gaussian from the accumulated statistics (float32 arithmetic, fixed order):
  *   c = count[i]; if c > 0: g = grad[i] / c, e = elev[i] / c (each one IEEE division)
  *   tau = tau_min + e * (tau_max - tau_min)   (one rounded product, one rounded sum)
- *   densify = c > 0 && g >= tau;  big = max(scales[i]) > percent_dense * scene_extent
+ *   densify = c > 0 && g >= tau;  big = max(scales[i]) > percent_dense * scene_extent (a float
+ *   product); prune = opacity[i] < min_opacity || (max_scale > 0 && max(scales[i]) > max_scale)
  *   action = prune ? ODGS_PRUNE : densify ? (big ? ODGS_SPLIT : ODGS_CLONE) : ODGS_KEEP
- * grad, elev: [n] float; count: [n] uint32; scales [n][3] and opacity [n] activated; action: [n]
- * bytes written. n >= 0. */
+ * grad, elev: [n] float; count: [n] uint32; scales [n][3] and opacity [n] (activated, or raw as
+ * described under raw_params); action: [n] bytes written. n >= 0. */
 odgs_status odgs_densify_select(const float *grad, const float *elev, const uint32_t *count,
                                 const float *scales, const float *opacity, int n,
                                 const odgs_densify_params *p, uint8_t *action, void *stream);
@@ -56,19 +62,52 @@ typedef struct {
 /* Bytes of scratch odgs_densify_apply needs for n Gaussians (host-only, pure). */
 odgs_status odgs_densify_scratch_size(int n, size_t *bytes);
 
-/* Builds the densified Gaussians from in (n Gaussians, sh_coeffs coefficients each) and action:
+/* Builds the densified Gaussians from in (n Gaussians, sh_coeffs coefficients each; log-scales
+ * when raw_params = 1) and action:
  *   [0, K)                 Gaussians with ODGS_KEEP or ODGS_CLONE, in index order
  *   [K, K + C)             the copies of the ODGS_CLONE ones, in index order
  *   [K + C, K + C + S)     the first children of the ODGS_SPLIT ones, in index order
  *   [K + C + S, K + C + 2S) their second children
  * A child c of Gaussian i sits at mu_i + R(q_i) (s_i * noise[i][c]) (noise: [n][2][3] standard
- * normal draws, read for split Gaussians only) with scales s_i / 1.6; rotation, opacity and SH
- * are copied. *n_out (device, one uint32) receives K + C + 2S; outputs at or beyond out_capacity
- * are not written (the caller compares *n_out with its capacity). The output arrays must not
+ * normal draws, read for split Gaussians only) with scales s_i / 1.6 (log-scales log s_i - ln 1.6
+ * when raw_params = 1); rotation, opacity and SH are copied. *n_out (device, one uint32)
+ * receives K + C + 2S; outputs at or beyond out_capacity are not written (the caller compares
+ * *n_out with its capacity). The output arrays must not
  * overlap the inputs. scratch: odgs_densify_scratch_size(n) bytes, 16-byte aligned. */
-odgs_status odgs_densify_apply(const odgs_gaussians *in, int sh_coeffs, const uint8_t *action,
-                               const float *noise, const odgs_params_out *out, int out_capacity,
-                               uint32_t *n_out, void *scratch, size_t scratch_bytes, void *stream);
+odgs_status odgs_densify_apply(const odgs_gaussians *in, int sh_coeffs, int raw_params,
+                               const uint8_t *action, const float *noise, const odgs_params_out *out,
+                               int out_capacity, uint32_t *n_out, void *scratch, size_t scratch_bytes,
+                               void *stream);
+
+/* Adam (Kingma & Ba 2015, bias-corrected), the optimiser ODGS trains with (App. A.1: the 3DGS
+ * recipe), over up to ODGS_ADAM_MAX_GROUPS groups of float32 parameters in one launch. Per
+ * element of a group, at step t >= 1:
+ *   m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2
+ *   p <- p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+ * with the bias corrections computed once on the host in double precision. Element j of a group
+ * uses lr when (j mod row) < head and lr_tail otherwise: with row = 3 K and head = 3 an SH array
+ * [n][K][3] gets 3DGS's separate rates for the DC and the higher-order coefficients.
+ * param, m, v: device arrays updated in place; grad: device array read; count elements each (no
+ * overlap between groups). m and v start at zero (step 1). */
+#define ODGS_ADAM_MAX_GROUPS 8
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m, *v;
+    size_t count;
+    float lr, lr_tail;
+    int row, head; /* row >= 1, 0 <= head <= row                                         */
+} odgs_adam_group;
+
+typedef struct {
+    double beta1, beta2;     /* 3DGS: 0.9, 0.999. Double, so that 1 - beta is formed before any
+                                rounding to float (1 - (float)0.999 is off by 1.3e-5 relative)  */
+    double eps;              /* 3DGS: 1e-15                                                   */
+    int step;                /* t >= 1                                                        */
+} odgs_adam_params;
+
+odgs_status odgs_adam_step(const odgs_adam_group *groups, int n_groups, const odgs_adam_params *p,
+                           void *stream);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,7 @@ class DensifyParams:
     scene_extent: float = 1.0
     min_opacity: float = 0.005
     max_scale: float = 0.0
+    raw_params: bool = False  # scales are log-scales, opacity logits
 
 
 def tau(one_minus_cos):
@@ -90,10 +91,19 @@ def select(grad, elev, count, scales, opacity, prm: DensifyParams):
     t = f(prm.tau_min) + emean * (f(prm.tau_max) - f(prm.tau_min))
     hot = seen & (gmean >= t)
     smax = np.max(np.asarray(scales, dtype=f), axis=1)
-    big = smax > f(prm.percent_dense) * f(prm.scene_extent)
-    prune = np.asarray(opacity, dtype=f) < f(prm.min_opacity)
-    if prm.max_scale > 0:
-        prune |= smax > f(prm.max_scale)
+    op = np.asarray(opacity, dtype=f)
+    if prm.raw_params:
+        # thresholds mapped into log-scale / logit space once, in double, then rounded to float
+        pd, ext, mo = (float(f(x)) for x in (prm.percent_dense, prm.scene_extent, prm.min_opacity))
+        big_thr = f(np.log(pd * ext))
+        op_thr = f(np.log(mo / (1.0 - mo))) if mo > 0 else f(-np.inf)
+        max_thr = f(np.log(float(f(prm.max_scale)))) if prm.max_scale > 0 else f(np.inf)
+    else:
+        big_thr = f(prm.percent_dense) * f(prm.scene_extent)
+        op_thr = f(prm.min_opacity)
+        max_thr = f(prm.max_scale) if prm.max_scale > 0 else f(np.inf)
+    big = smax > big_thr
+    prune = (op < op_thr) | (smax > max_thr)
     act = np.where(hot, np.where(big, SPLIT, CLONE), KEEP)
     return np.where(prune, PRUNE, act).astype(np.uint8)
 
@@ -109,8 +119,9 @@ def _rotation(q):
         np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
 
 
-def apply(means, scales, quats, opacity, sh, action, noise):
-    """New parameter arrays (FP64) after cloning, splitting and pruning; noise is [n, 2, 3]."""
+def apply(means, scales, quats, opacity, sh, action, noise, raw_params=False):
+    """New parameter arrays (FP64) after cloning, splitting and pruning; noise is [n, 2, 3].
+    With raw_params the scales are log-scales: children get log s - ln 1.6."""
     action = np.asarray(action)
     keep = (action == KEEP) | (action == CLONE)
     clone = action == CLONE
@@ -119,7 +130,7 @@ def apply(means, scales, quats, opacity, sh, action, noise):
     out = [np.concatenate([a[keep], a[clone], a[split], a[split]]) for a in arrays]
     if split.any():
         R = _rotation(arrays[2][split])
-        s = arrays[1][split]
+        s = np.exp(arrays[1][split]) if raw_params else arrays[1][split]
         mu = arrays[0][split]
         kids = []
         for c in range(2):
@@ -128,5 +139,5 @@ def apply(means, scales, quats, opacity, sh, action, noise):
         nk, nc, ns = int(keep.sum()), int(clone.sum()), int(split.sum())
         out[0][nk + nc:nk + nc + ns] = kids[0]
         out[0][nk + nc + ns:] = kids[1]
-        out[1][nk + nc:] = out[1][nk + nc:] / 1.6
+        out[1][nk + nc:] = out[1][nk + nc:] - np.log(1.6) if raw_params else out[1][nk + nc:] / 1.6
     return out

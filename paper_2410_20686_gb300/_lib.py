@@ -24,7 +24,7 @@ EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buf
             "odgs_preprocess", "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd",
             "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
             "odgs_render_fwd_static", "odgs_measure_peaks", "odgs_last_launch_count", "odgs_status_string",
-            "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply")
+            "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply", "odgs_adam_step")
 
 
 class OdgsError(RuntimeError):
@@ -41,7 +41,7 @@ class Settings(C.Structure):
     _fields_ = [("sh_degree", C.c_int), ("sh_coeffs", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int),
                 ("batch", C.c_int), ("cov_dilation", C.c_float), ("r_near", C.c_float), ("r_far", C.c_float),
                 ("bg", C.c_float * 3), ("recompute_lists", C.c_int), ("grad_accumulate", C.c_int),
-                ("pixels_per_thread", C.c_int)]
+                ("pixels_per_thread", C.c_int), ("raw_params", C.c_int)]
 
 
 class Gaussians(C.Structure):
@@ -57,12 +57,23 @@ class Stats(C.Structure):
 
 class DensifyParams(C.Structure):
     _fields_ = [("tau_min", C.c_float), ("tau_max", C.c_float), ("percent_dense", C.c_float),
-                ("scene_extent", C.c_float), ("min_opacity", C.c_float), ("max_scale", C.c_float)]
+                ("scene_extent", C.c_float), ("min_opacity", C.c_float), ("max_scale", C.c_float),
+                ("raw_params", C.c_int)]
 
 
 class ParamsOut(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class AdamGroup(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("count", C.c_size_t), ("lr", C.c_float), ("lr_tail", C.c_float), ("row", C.c_int),
+                ("head", C.c_int)]
+
+
+class AdamParams(C.Structure):
+    _fields_ = [("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double), ("step", C.c_int)]
 
 
 class Peaks(C.Structure):
@@ -106,8 +117,9 @@ def load(path: str = LIB_PATH):
     L.odgs_measure_peaks.argtypes = [C.POINTER(Peaks), vp]
     L.odgs_densify_select.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.POINTER(DensifyParams), vp, vp]
     L.odgs_densify_scratch_size.argtypes = [C.c_int, C.POINTER(sz)]
-    L.odgs_densify_apply.argtypes = [C.POINTER(Gaussians), C.c_int, vp, vp, C.POINTER(ParamsOut), C.c_int, vp, vp,
-                                     sz, vp]
+    L.odgs_adam_step.argtypes = [C.POINTER(AdamGroup), C.c_int, C.POINTER(AdamParams), vp]
+    L.odgs_densify_apply.argtypes = [C.POINTER(Gaussians), C.c_int, C.c_int, vp, vp, C.POINTER(ParamsOut), C.c_int,
+                                     vp, vp, sz, vp]
     L.odgs_last_launch_count.argtypes = [vp]
     L.odgs_last_launch_count.restype = C.c_int
     L.odgs_status_string.argtypes = [C.c_int]
@@ -115,7 +127,8 @@ def load(path: str = LIB_PATH):
     for name in ("odgs_create", "odgs_workspace_size", "odgs_pair_buffer_size", "odgs_preprocess",
                  "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
                  "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static",
-                 "odgs_measure_peaks", "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply"):
+                 "odgs_measure_peaks", "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply",
+                 "odgs_adam_step"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

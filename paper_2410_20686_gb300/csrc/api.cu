@@ -101,6 +101,7 @@ odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
     if (!finite(t.r_near) || !(t.r_far > t.r_near) || t.r_near < 0.f) return ODGS_ERR_INVALID_ARG;
     for (int c = 0; c < 3; ++c)
         if (!finite(t.bg[c])) return ODGS_ERR_INVALID_ARG;
+    if (t.raw_params != 0 && t.raw_params != 1) return ODGS_ERR_INVALID_ARG;
     *out = t;
     return ODGS_OK;
 }
@@ -239,6 +240,7 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.st.tile_w = c->s.tile_w; a.st.tile_h = c->s.tile_h;
     a.st.dilation = c->s.cov_dilation; a.st.r_near = c->s.r_near; a.st.r_far = c->s.r_far;
     for (int i = 0; i < 3; ++i) a.st.bg[i] = c->s.bg[i];
+    a.st.raw = c->s.raw_params;
     a.rec_a = reinterpret_cast<float4*>(w + c->L.rec_a);
     a.rec_b = reinterpret_cast<float4*>(w + c->L.rec_b);
     a.rec_c = reinterpret_cast<float4*>(w + c->L.rec_c);
@@ -495,6 +497,7 @@ odgs_status odgs_preprocess_bwd(odgs_ctx* c, const odgs_grads* grads, void* stre
     b.g_means = grads->means; b.g_scales = grads->scales; b.g_quats = grads->quats;
     b.g_opacity = grads->opacity; b.g_sh = grads->sh;
     b.accumulate = c->s.grad_accumulate;
+    b.raw = c->s.raw_params;
     if (launch_preprocess_bwd(b, c->s.sh_degree, st) != cudaSuccess) return ODGS_ERR_CUDA;
     if (c->n > 0) c->launches += 1;
     return ODGS_OK;

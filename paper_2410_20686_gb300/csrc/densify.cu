@@ -12,6 +12,8 @@
 // point is to keep the parameters on the device, not to reach the copy bandwidth.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "odgs_common.cuh"
 #include "odgs_train.h"
 
@@ -21,13 +23,15 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPerThread = 4;
 constexpr int kTile = kThreads * kPerThread;
+constexpr float kLog1p6 = 0.470003629245735553650937f;  // ln 1.6: log-scale of a split child
 
 __global__ void __launch_bounds__(kThreads) k_densify_select(const float* __restrict__ grad,
                                                              const float* __restrict__ elev,
                                                              const uint32_t* __restrict__ count,
                                                              const float* __restrict__ scales,
                                                              const float* __restrict__ opacity, int n,
-                                                             odgs_densify_params p, uint8_t* __restrict__ action) {
+                                                             odgs_densify_params p, float big_thr, float op_thr,
+                                                             float max_thr, uint8_t* __restrict__ action) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t c = count[i];
@@ -41,8 +45,9 @@ __global__ void __launch_bounds__(kThreads) k_densify_select(const float* __rest
     const float tau = __fadd_rn(p.tau_min, __fmul_rn(emean, __fsub_rn(p.tau_max, p.tau_min)));
     const bool hot = c > 0u && gmean >= tau;
     const float smax = fmaxf(fmaxf(scales[3 * i], scales[3 * i + 1]), scales[3 * i + 2]);
-    const bool big = smax > __fmul_rn(p.percent_dense, p.scene_extent);
-    const bool prune = opacity[i] < p.min_opacity || (p.max_scale > 0.f && smax > p.max_scale);
+    // thresholds in the space of the inputs (activated, or log-scale / logit), set by the host
+    const bool big = smax > big_thr;
+    const bool prune = opacity[i] < op_thr || smax > max_thr;
     action[i] = (uint8_t)(prune ? ODGS_PRUNE : hot ? (big ? ODGS_SPLIT : ODGS_CLONE) : ODGS_KEEP);
 }
 
@@ -138,6 +143,7 @@ struct ApplyArgs {
     const uint4* tile_offsets;
     const uint4* totals;
     uint32_t* src;  // [cap] source Gaussian of every output slot
+    int raw;        // scales are log-scales
 };
 
 // Copies Gaussian i into slot d (d < cap); child >= 0 places it as that split child.
@@ -147,6 +153,10 @@ __device__ __forceinline__ void write_gaussian(const ApplyArgs& a, int i, uint32
     float m[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
     float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
     if (child >= 0) {
+        if (a.raw) {  // the child's offset uses the activated scales
+#pragma unroll
+            for (int r = 0; r < 3; ++r) s[r] = expf(s[r]);
+        }
         const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
         float R[9];
         quat_rot(q.x / qn, q.y / qn, q.z / qn, q.w / qn, R);
@@ -154,8 +164,13 @@ __device__ __forceinline__ void write_gaussian(const ApplyArgs& a, int i, uint32
         const float sz[3] = {s[0] * z[0], s[1] * z[1], s[2] * z[2]};
 #pragma unroll
         for (int r = 0; r < 3; ++r) m[r] += R[3 * r] * sz[0] + R[3 * r + 1] * sz[1] + R[3 * r + 2] * sz[2];
+        if (a.raw) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) s[r] = __fdiv_rn(s[r], 1.6f);
+            for (int r = 0; r < 3; ++r) s[r] = __fsub_rn(a.scales[3 * i + r], kLog1p6);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) s[r] = __fdiv_rn(s[r], 1.6f);
+        }
     }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -235,8 +250,21 @@ extern "C" odgs_status odgs_densify_select(const float* grad, const float* elev,
     if (n == 0) return ODGS_OK;
     if (!grad || !elev || !count || !scales || !opacity || !action) return ODGS_ERR_INVALID_ARG;
     if (!(p->scene_extent > 0.f) || !(p->tau_max >= p->tau_min) || p->max_scale < 0.f) return ODGS_ERR_INVALID_ARG;
+    if (p->raw_params != 0 && p->raw_params != 1) return ODGS_ERR_INVALID_ARG;
+    if (!(p->min_opacity >= 0.f && p->min_opacity < 1.f)) return ODGS_ERR_INVALID_ARG;
+    const float inf = INFINITY;
+    float big_thr, op_thr, max_thr;
+    if (p->raw_params) {
+        big_thr = (float)std::log((double)p->percent_dense * (double)p->scene_extent);
+        op_thr = p->min_opacity > 0.f ? (float)std::log((double)p->min_opacity / (1.0 - (double)p->min_opacity)) : -inf;
+        max_thr = p->max_scale > 0.f ? (float)std::log((double)p->max_scale) : inf;
+    } else {
+        big_thr = p->percent_dense * p->scene_extent;  // one float product, as the oracle takes it
+        op_thr = p->min_opacity;
+        max_thr = p->max_scale > 0.f ? p->max_scale : inf;
+    }
     k_densify_select<<<(n + kThreads - 1) / kThreads, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-        grad, elev, count, scales, opacity, n, *p, action);
+        grad, elev, count, scales, opacity, n, *p, big_thr, op_thr, max_thr, action);
     return cudaGetLastError() == cudaSuccess ? ODGS_OK : ODGS_ERR_CUDA;
 }
 
@@ -246,10 +274,12 @@ extern "C" odgs_status odgs_densify_scratch_size(int n, size_t* bytes) {
     return ODGS_OK;
 }
 
-extern "C" odgs_status odgs_densify_apply(const odgs_gaussians* in, int sh_coeffs, const uint8_t* action,
-                                          const float* noise, const odgs_params_out* out, int out_capacity,
-                                          uint32_t* n_out, void* scratch, size_t scratch_bytes, void* stream) {
+extern "C" odgs_status odgs_densify_apply(const odgs_gaussians* in, int sh_coeffs, int raw_params,
+                                          const uint8_t* action, const float* noise, const odgs_params_out* out,
+                                          int out_capacity, uint32_t* n_out, void* scratch, size_t scratch_bytes,
+                                          void* stream) {
     if (!in || !out || !n_out || in->n < 0 || sh_coeffs < 1 || out_capacity < 0) return ODGS_ERR_INVALID_ARG;
+    if (raw_params != 0 && raw_params != 1) return ODGS_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int n = in->n;
     if (n == 0) return cudaMemsetAsync(n_out, 0, sizeof(uint32_t), st) == cudaSuccess ? ODGS_OK : ODGS_ERR_CUDA;
@@ -272,6 +302,7 @@ extern "C" odgs_status odgs_densify_apply(const odgs_gaussians* in, int sh_coeff
     a.n = n; a.sh_coeffs = sh_coeffs; a.action = action; a.noise = noise;
     a.o_means = out->means; a.o_scales = out->scales; a.o_quats = out->quats; a.o_opacity = out->opacity;
     a.o_sh = out->sh; a.cap = cap; a.tile_offsets = tile_offsets; a.totals = totals; a.src = src;
+    a.raw = raw_params;
     k_apply_scatter<<<tiles, kThreads, 0, st>>>(a);
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -67,7 +67,12 @@ struct Settings {
     int tile_w, tile_h;
     float dilation, r_near, r_far;
     float bg[3];
+    int raw;  // scales are log-scales and opacity logits
 };
+
+// Activation of the raw variables of 3DGS training: scale = exp(log-scale), opacity =
+// sigmoid(logit) = 1 / (1 + exp(-logit)).
+__device__ __forceinline__ float sigmoid_act(float x) { return 1.f / (1.f + expf(-x)); }
 
 // ------------------------------------------------------------------ float-float arithmetic
 // Unevaluated sums hi + lo (Dekker 1971; Knuth's TwoSum), used only to place the ERP mean

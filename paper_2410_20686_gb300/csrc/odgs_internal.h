@@ -35,6 +35,7 @@ struct PreBwdArgs {
     const float4* acc;
     float *g_means, *g_scales, *g_quats, *g_opacity, *g_sh;
     int accumulate;
+    int raw;                         // gradients w.r.t. log-scales and opacity logits
     const uint4* rect;               // footprint words: tile count > 0 <=> visible in that view
     float *d_grad, *d_elev;          // densification statistics (all three or none)
     uint32_t* d_count;

@@ -215,9 +215,13 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
     uint32_t local_visible = 0u;
     if (g < a.n) {
         const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
-        const float s0 = __ldg(a.scales + 3 * g), s1 = __ldg(a.scales + 3 * g + 1), s2 = __ldg(a.scales + 3 * g + 2);
+        float s0 = __ldg(a.scales + 3 * g), s1 = __ldg(a.scales + 3 * g + 1), s2 = __ldg(a.scales + 3 * g + 2);
         const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
-        const float o = __ldg(a.opacity + g);
+        float o = __ldg(a.opacity + g);
+        if (a.st.raw) {
+            s0 = expf(s0); s1 = expf(s1); s2 = expf(s2);
+            o = sigmoid_act(o);
+        }
 
         // Sigma = M M^T with M = R(q) S (Sec. 3.1)
         float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
@@ -371,7 +375,11 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.n) return;
     const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
-    const float s[3] = {__ldg(a.scales + 3 * g), __ldg(a.scales + 3 * g + 1), __ldg(a.scales + 3 * g + 2)};
+    float s[3] = {__ldg(a.scales + 3 * g), __ldg(a.scales + 3 * g + 1), __ldg(a.scales + 3 * g + 2)};
+    if (a.raw) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[i] = expf(s[i]);
+    }
     const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
 
     float gm[3] = {0.f, 0.f, 0.f}, gop = 0.f;
@@ -559,6 +567,12 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         float dot = qw * dw + qx * dx + qy * dy + qz * dz;
         gq[0] = (dw - qw * dot) / qn; gq[1] = (dx - qx * dot) / qn;
         gq[2] = (dy - qy * dot) / qn; gq[3] = (dz - qz * dot) / qn;
+    }
+    if (a.raw) {  // chain through the activations: d/dlog s = d/ds * s, d/dlogit = d/do * o (1 - o)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gs[i] *= s[i];
+        const float o = sigmoid_act(__ldg(a.opacity + g));
+        gop *= o * (1.f - o);
     }
     // write (or accumulate) the parameter gradients
     float* pm = a.g_means + 3 * g;

@@ -35,10 +35,11 @@ class DensifyParams:
     scene_extent: float = 1.0
     min_opacity: float = 0.005
     max_scale: float = 0.0
+    raw_params: bool = False  # scales are log-scales and opacity logits
 
     def to_c(self) -> L.DensifyParams:
         return L.DensifyParams(self.tau_min, self.tau_max, self.percent_dense, self.scene_extent, self.min_opacity,
-                               self.max_scale)
+                               self.max_scale, int(bool(self.raw_params)))
 
 
 class DensifyStats:
@@ -76,9 +77,10 @@ def select(stats: DensifyStats, scales: torch.Tensor, opacity: torch.Tensor,
     return action
 
 
-def apply(means, scales, quats, opacity, sh, action, noise=None, generator=None):
+def apply(means, scales, quats, opacity, sh, action, noise=None, generator=None, raw_params=False):
     """Densified (means, scales, quats, opacity, sh). noise: [n, 2, 3] standard normal draws for
-    the split children (drawn with ``generator`` when None). Synchronizes once to read the count."""
+    the split children (drawn with ``generator`` when None). raw_params: scales are log-scales.
+    Synchronizes once to read the count."""
     n = means.shape[0]
     dev = means.device
     if noise is None:
@@ -100,7 +102,8 @@ def apply(means, scales, quats, opacity, sh, action, noise=None, generator=None)
     n_out = torch.zeros(1, dtype=torch.int32, device=dev)
     g = L.Gaussians(_ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity), _ptr(sh), int(n))
     o = L.ParamsOut(*[_ptr(t) for t in out])
-    L.check(lib.odgs_densify_apply(C.byref(g), int(k), _ptr(action), _ptr(noise), C.byref(o), int(cap),
+    L.check(lib.odgs_densify_apply(C.byref(g), int(k), int(bool(raw_params)), _ptr(action), _ptr(noise), C.byref(o),
+                                   int(cap),
                                    _ptr(n_out), _ptr(scratch), C.c_size_t(scratch.numel()), _stream(dev)),
             "odgs_densify_apply")
     m = int(n_out.item())

@@ -27,6 +27,7 @@ class RenderSettings:
     recompute_lists: bool = False
     grad_accumulate: bool = False
     pixels_per_thread: int = 0
+    raw_params: bool = False  # scales are log-scales and opacity logits (activated by the kernels)
 
     def c_struct(self, sh_coeffs: int) -> L.Settings:
         s = L.Settings()
@@ -37,6 +38,7 @@ class RenderSettings:
         s.recompute_lists = int(bool(self.recompute_lists))
         s.grad_accumulate = int(bool(self.grad_accumulate))
         s.pixels_per_thread = int(self.pixels_per_thread)
+        s.raw_params = int(bool(self.raw_params))
         return s
 
 

@@ -144,3 +144,34 @@ def test_apply_clones_splits_and_prunes():
             Sig = R @ np.diag(scales[i] ** 2) @ R.T
             d = out[0][7 + 2 * c + j] - means[i]
             assert d @ np.linalg.solve(Sig, d) == pytest.approx(noise[i, c] @ noise[i, c], rel=1e-10)
+
+
+def test_raw_parameter_mode_agrees_with_activated_mode():
+    # log-scales and opacity logits: the same decisions away from the thresholds, and children whose
+    # activated scales are the activated mode's children
+    rng = np.random.default_rng(3)
+    n = 4000
+    count = rng.integers(1, 5, n).astype(np.uint32)
+    elev = (rng.uniform(0, 1, n) * count).astype(np.float32)
+    grad = (rng.uniform(0, 2e-4, n) * count).astype(np.float32)
+    scales = rng.uniform(5e-4, 6e-3, (n, 3))
+    opac = rng.uniform(0.0, 0.02, n)
+    prm = D.DensifyParams(scene_extent=2.0, max_scale=5e-3)
+    raw = D.DensifyParams(scene_extent=2.0, max_scale=5e-3, raw_params=True)
+    a = D.select(grad, elev, count, scales.astype(np.float32), opac.astype(np.float32), prm)
+    b = D.select(grad, elev, count, np.log(scales).astype(np.float32),
+                 np.log(opac / (1 - opac)).astype(np.float32), raw)
+    smax = scales.max(axis=1)
+    far = (np.abs(smax / 2e-3 - 1) > 1e-5) & (np.abs(smax / 5e-3 - 1) > 1e-5) & (np.abs(opac / 0.005 - 1) > 1e-5)
+    np.testing.assert_array_equal(a[far], b[far])
+    assert far.mean() > 0.99
+    q = rng.normal(size=(n, 4))
+    mu = rng.normal(size=(n, 3))
+    sh = rng.normal(size=(n, 1, 3))
+    noise = rng.normal(size=(n, 2, 3))
+    act = a.copy()
+    act[act == D.PRUNE] = D.SPLIT
+    x = D.apply(mu, scales, q, opac, sh, act, noise)
+    y = D.apply(mu, np.log(scales), q, opac, sh, act, noise, raw_params=True)
+    np.testing.assert_allclose(x[0], y[0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(x[1], np.exp(y[1]), rtol=1e-12)
