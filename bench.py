@@ -408,6 +408,25 @@ def run_adam(torch, dev, params, hbm_gbs, iters=10):
             "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_gbs, "l2": "inputs (1.65 GB) larger than L2, flushed too"}
 
 
+def run_loss(torch, dev, image, target, hbm_gbs, alu_tflops, iters=20):
+    """L1 + D-SSIM loss and gradient of the 2048x1024 view (cos-theta row weights, seam wrap)."""
+    from paper_2410_20686_gb300.loss import l1_dssim
+    l1_dssim([image], [target])
+    ms = timed_flushed(torch, dev, lambda: l1_dssim([image], [target]), iters)
+    px = image.numel() // 3
+    # algorithmic: image and target read, gradient written (36 B per pixel); the kernels also write
+    # and re-read three adjoint maps per channel (another 72 B per pixel)
+    nbytes = px * 36
+    # 11-tap separable passes: forward 5 moments x 11 taps x (26 / 16 halo rows + 1), backward 3 x 11
+    # x (26 / 16 + 1), per channel, 2 flop each; the per-pixel SSIM terms are left out
+    flops = px * 3 * 2 * (5 + 3) * 11 * (26.0 / 16.0 + 1.0)
+    t = ms * 1e-3
+    return {"workload": "L1 + D-SSIM (lambda 0.2, 11x11 window) and its gradient on one 2048x1024 ERP view",
+            "ms": ms, "gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / hbm_gbs,
+            "tflops": flops / t / 1e12, "alu_frac": flops / t / 1e12 / alu_tflops,
+            "traffic_per_pixel_bytes": 108, "l2": "flushed before every timed call"}
+
+
 # ------------------------------------------------------------------ multi-process plumbing
 
 def dist_env():
@@ -592,8 +611,11 @@ def run_ours(args):
     if not args.no_batched:
         out["batched"] = run_batched(dev, rs, args.batched_steps, args.warmup)
     if not args.no_next:
+        imgs_last, _ = rast.forward(*params, [view], rs, want_T=False)
+        imgs_last = imgs_last[0]
         out["next"] = {"densify": run_densify(torch, dev, rast, params, view, rs, target, float(peaks["hbm_gbs"])),
-                       "adam": run_adam(torch, dev, params, float(peaks["hbm_gbs"]))}
+                       "adam": run_adam(torch, dev, params, float(peaks["hbm_gbs"])),
+                       "loss": run_loss(torch, dev, imgs_last, target, float(peaks["hbm_gbs"]), peak_tf)}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(out), flush=True)

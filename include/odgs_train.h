@@ -109,6 +109,30 @@ typedef struct {
 odgs_status odgs_adam_step(const odgs_adam_group *groups, int n_groups, const odgs_adam_params *p,
                            void *stream);
 
+/* Photometric loss of 3DGS training on one ERP image (App. A.1 keeps the 3DGS loss):
+ *   L = (1 - lambda) L1 + lambda (1 - SSIM),
+ * SSIM of Wang et al. 2004 with an 11 x 11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2,
+ * per channel. Both terms are means over the 3 x W x H values, weighted per pixel row by
+ * cos(theta_j) when area_weight = 1 (theta_j = pi (1/2 - (j + 1/2) / H), Eq. 4's elevation of
+ * the row centre: the solid angle of the row). The window wraps around the longitude seam when
+ * wrap_u = 1 (zero padding otherwise) and is zero-padded above and below the image.
+ * image, target: device [3][H][W] float32. grad: device [3][H][W], receives dL/dimage (the L1
+ * term's derivative at image == target is 0); may be NULL. loss: device float, receives L (or L
+ * is added to it when accumulate = 1, so that views sum into one value). scratch:
+ * odgs_loss_scratch_size bytes, 16-byte aligned, reused by every call on the same stream. */
+typedef struct {
+    float lambda;    /* D-SSIM weight; 3DGS: 0.2                          */
+    int area_weight; /* 1: cos(theta) row weights                         */
+    int wrap_u;      /* 1: the window wraps around the seam               */
+    int accumulate;  /* 1: *loss += L; 0: *loss = L                       */
+} odgs_loss_params;
+
+odgs_status odgs_loss_scratch_size(int width, int height, size_t *bytes);
+
+odgs_status odgs_loss_l1_dssim(const float *image, const float *target, int width, int height,
+                               const odgs_loss_params *p, float *grad, float *loss, void *scratch,
+                               size_t scratch_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

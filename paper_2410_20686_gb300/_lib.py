@@ -24,7 +24,8 @@ EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buf
             "odgs_preprocess", "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd",
             "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
             "odgs_render_fwd_static", "odgs_measure_peaks", "odgs_last_launch_count", "odgs_status_string",
-            "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply", "odgs_adam_step")
+            "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply", "odgs_adam_step",
+            "odgs_loss_scratch_size", "odgs_loss_l1_dssim")
 
 
 class OdgsError(RuntimeError):
@@ -76,6 +77,10 @@ class AdamParams(C.Structure):
     _fields_ = [("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double), ("step", C.c_int)]
 
 
+class LossParams(C.Structure):
+    _fields_ = [("lambda_", C.c_float), ("area_weight", C.c_int), ("wrap_u", C.c_int), ("accumulate", C.c_int)]
+
+
 class Peaks(C.Structure):
     _fields_ = [("ffma_tflops", C.c_double), ("ex2_gops", C.c_double), ("sms", C.c_int)]
 
@@ -118,6 +123,8 @@ def load(path: str = LIB_PATH):
     L.odgs_densify_select.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.POINTER(DensifyParams), vp, vp]
     L.odgs_densify_scratch_size.argtypes = [C.c_int, C.POINTER(sz)]
     L.odgs_adam_step.argtypes = [C.POINTER(AdamGroup), C.c_int, C.POINTER(AdamParams), vp]
+    L.odgs_loss_scratch_size.argtypes = [C.c_int, C.c_int, C.POINTER(sz)]
+    L.odgs_loss_l1_dssim.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(LossParams), vp, vp, vp, sz, vp]
     L.odgs_densify_apply.argtypes = [C.POINTER(Gaussians), C.c_int, C.c_int, vp, vp, C.POINTER(ParamsOut), C.c_int,
                                      vp, vp, sz, vp]
     L.odgs_last_launch_count.argtypes = [vp]
@@ -128,7 +135,7 @@ def load(path: str = LIB_PATH):
                  "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
                  "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static",
                  "odgs_measure_peaks", "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply",
-                 "odgs_adam_step"):
+                 "odgs_adam_step", "odgs_loss_scratch_size", "odgs_loss_l1_dssim"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
