@@ -55,6 +55,8 @@ typedef struct {
     int width, height;
     double R[9]; /* world -> camera rotation W, row-major */
     double t[3]; /* world -> camera translation */
+    int model;   /* 0: ERP (Eq. 4); 1: pinhole, u = fx tx/tz + cx, v = fy ty/tz + cy (Eq. 1) */
+    double fx, fy, cx, cy; /* pinhole only */
 } orc_view;
 
 typedef struct {
@@ -209,6 +211,7 @@ static float depth_key_f32(const double *mu, const orc_view *v)
         s = s + (float)v->t[i];
         t[i] = s;
     }
+    if (v->model == 1) return t[2]; /* pinhole: the z depth, as perspective 3DGS sorts */
     float xx = t[0] * t[0];
     float yy = t[1] * t[1];
     float zz = t[2] * t[2];
@@ -255,6 +258,22 @@ static void project_one(const double *mean, const double *scale, const double *q
     double r = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     double rho = sqrt(t[0] * t[0] + t[2] * t[2]);
     pj[PJ_R] = r;
+    double J[6];
+    if (v->model == 1) {
+        /* pinhole (the perspective case of Sec. 3.1, Eq. 1): near / far planes on the float z
+         * depth; centres outside the image widened by 30 % on each side are culled */
+        if (!((double)rf > s->r_near && (double)rf < s->r_far)) return;
+        double tz = t[2];
+        double u = v->fx * t[0] / tz + v->cx, vv = v->fy * t[1] / tz + v->cy;
+        if (!(u >= -0.3 * W && u <= 1.3 * W && vv >= -0.3 * H && vv <= 1.3 * H)) return;
+        pj[PJ_PHI] = atan2(t[0], t[2]);
+        pj[PJ_THETA] = atan2(-t[1], rho);
+        pj[PJ_U] = u;
+        pj[PJ_V] = vv;
+        J[0] = v->fx / tz; J[1] = 0.0; J[2] = -v->fx * t[0] / (tz * tz);
+        J[3] = 0.0; J[4] = v->fy / tz; J[5] = -v->fy * t[1] / (tz * tz);
+        goto have_jacobian;
+    }
     /* spherical-shell culling (Sec. 3.2) on the single-precision depth; poles culled */
     if (!((double)rf > s->r_near && (double)rf < s->r_far)) return;
     if (!(rho > 1e-4 * r)) return;
@@ -284,13 +303,13 @@ static void project_one(const double *mean, const double *scale, const double *q
     double SQJ[6];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 3; ++j) SQJ[3 * i + j] = SQ[2 * i] * Jo[j] + SQ[2 * i + 1] * Jo[3 + j];
-    double J[6];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 3; ++j) {
             double acc = 0;
             for (int k = 0; k < 3; ++k) acc += SQJ[3 * i + k] * Tmu[3 * k + j];
             J[3 * i + j] = acc;
         }
+have_jacobian:
     memcpy(pj + PJ_J, J, sizeof(J));
 
     /* Sigma_2D = T Sigma T^T with T = J W (Sec. 3.2 / App. A.3), plus the dilation */
@@ -397,11 +416,12 @@ static sorted_g *sort_visible(int n, const double *pj, int *m_out)
 #define ALPHA_MAX 0.99
 #define T_MIN 1e-4
 
-/* Offset from the Gaussian's centre to the pixel, horizontal part wrapped to [-W/2, W/2). */
+/* Offset from the Gaussian's centre to the pixel; for ERP views (W > 0) the horizontal part is
+ * wrapped to [-W/2, W/2); pinhole views pass W = 0 (no wrap). */
 static void pixel_offset(double px, double py, double u, double v, int W, double *dx, double *dy)
 {
     double d = px - u;
-    *dx = d - (double)W * floor(d / (double)W + 0.5);
+    *dx = W > 0 ? d - (double)W * floor(d / (double)W + 0.5) : d;
     *dy = py - v;
 }
 
@@ -471,7 +491,8 @@ int orc_render(int n, const double *means, const double *scales, const double *q
         int flat = pix ? pix[p] : p;
         int x = flat % v->width, y = flat / v->width;
         double T;
-        int nc = blend_pixel(g, m, x + s->pix_offset, y + s->pix_offset, v->width, s, color + 3 * (size_t)p,
+        int nc = blend_pixel(g, m, x + s->pix_offset, y + s->pix_offset, v->model == 1 ? 0 : v->width, s,
+                             color + 3 * (size_t)p,
                              &T, margins ? margins + 3 * (size_t)p : NULL, NULL, 0);
         final_T[p] = T;
         if (ncontrib) ncontrib[p] = nc;
@@ -582,6 +603,19 @@ static void project_adjoint(const double *mean, const double *scale, const doubl
             dSig[3 * i + j] = acc;
         }
 
+    double dt[3];
+    if (v->model == 1) {
+        /* pinhole: u = fx tx/tz + cx, v = fy ty/tz + cy; J = [[fx/tz, 0, -fx tx/tz^2],
+         * [0, fy/tz, -fy ty/tz^2]] (Eq. 1), differentiated w.r.t. t */
+        const double *tp = pj + PJ_T;
+        double tx = tp[0], ty = tp[1], tz = tp[2], iz = 1.0 / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        double pfx = v->fx, pfy = v->fy;
+        dt[0] = g2[G2_U] * pfx * iz - dJ[2] * pfx * iz2;
+        dt[1] = g2[G2_V] * pfy * iz - dJ[5] * pfy * iz2;
+        dt[2] = -g2[G2_U] * pfx * tx * iz2 - g2[G2_V] * pfy * ty * iz2 - dJ[0] * pfx * iz2
+                + dJ[2] * 2.0 * pfx * tx * iz3 - dJ[4] * pfy * iz2 + dJ[5] * 2.0 * pfy * ty * iz3;
+        goto have_dt;
+    }
     /* J_omni as a function of (r, theta, phi):
      *   J11 = fx cos(phi) / (r cos(theta)), J13 = -fx sin(phi) / (r cos(theta)),
      *   J21 = fy sin(theta) sin(phi) / r, J22 = fy cos(theta) / r, J23 = fy sin(theta) cos(phi) / r */
@@ -601,8 +635,8 @@ static void project_adjoint(const double *mean, const double *scale, const doubl
     double drdt[3] = {t[0] / r, t[1] / r, t[2] / r};
     double dphdt[3] = {t[2] / rho2, 0.0, -t[0] / rho2};
     double dthdt[3] = {t[0] * t[1] / (r2 * rho), -rho / r2, t[2] * t[1] / (r2 * rho)};
-    double dt[3];
     for (int k = 0; k < 3; ++k) dt[k] = dLdr * drdt[k] + dLdth * dthdt[k] + dLdph * dphdt[k];
+have_dt:
     /* t = W mu + t_wc  ->  dL/dmu = W^T dL/dt */
     for (int j = 0; j < 3; ++j) gm[j] += v->R[j] * dt[0] + v->R[3 + j] * dt[1] + v->R[6 + j] * dt[2];
 
@@ -687,7 +721,8 @@ int orc_backward(int n, const double *means, const double *scales, const double 
             if (d[0] == 0.0 && d[1] == 0.0 && d[2] == 0.0) continue;
             int flat = pix ? pix[p] : p;
             int x = flat % v->width, y = flat / v->width;
-            blend_pixel_adjoint(g, m, x + s->pix_offset, y + s->pix_offset, v->width, s, d, g2, list, m);
+            blend_pixel_adjoint(g, m, x + s->pix_offset, y + s->pix_offset, v->model == 1 ? 0 : v->width, s, d, g2,
+                                list, m);
         }
         free(list);
     }

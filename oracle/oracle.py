@@ -34,7 +34,8 @@ def build(force: bool = False) -> str:
 
 
 class _View(C.Structure):
-    _fields_ = [("width", C.c_int), ("height", C.c_int), ("R", C.c_double * 9), ("t", C.c_double * 3)]
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("R", C.c_double * 9), ("t", C.c_double * 3),
+                ("model", C.c_int), ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double)]
 
 
 class _Settings(C.Structure):
@@ -92,6 +93,8 @@ def _cview(view):
     v.width, v.height = int(view.width), int(view.height)
     v.R[:] = [float(x) for x in np.asarray(view.R_wc, dtype=np.float64).ravel()]
     v.t[:] = [float(x) for x in np.asarray(view.t_wc, dtype=np.float64).ravel()]
+    v.model = int(getattr(view, "model", 0))
+    v.fx, v.fy, v.cx, v.cy = (float(getattr(view, k, 0.0)) for k in ("fx", "fy", "cx", "cy"))
     return v
 
 

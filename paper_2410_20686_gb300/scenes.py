@@ -30,6 +30,11 @@ class View:
     height: int
     R_wc: np.ndarray  # [3, 3] float32, world -> camera rotation (row-major)
     t_wc: np.ndarray  # [3] float32
+    model: int = 0    # 0: ERP; 1: pinhole with focal lengths fx, fy and principal point cx, cy (pixels)
+    fx: float = 0.0
+    fy: float = 0.0
+    cx: float = 0.0
+    cy: float = 0.0
 
     @staticmethod
     def identity(width: int, height: int, center=(0.0, 0.0, 0.0)) -> "View":
@@ -94,6 +99,37 @@ def _pack(means, scales, quats, opacity, sh, deg, views, name, recompute=False) 
 def _unit_vectors(rng, n):
     v = rng.normal(size=(n, 3))
     return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def pinhole_view(width, height, fx, fy, cx=None, cy=None, R_wc=None, t_wc=None) -> View:
+    """Pinhole camera: pixel (i, j) is sampled at (i + 1/2, j + 1/2) of the plane
+    u = fx tx / tz + cx, v = fy ty / tz + cy (principal point at the image centre by default)."""
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    return View(width, height, np.eye(3, dtype=np.float32) if R_wc is None else np.asarray(R_wc, np.float32),
+                np.zeros(3, np.float32) if t_wc is None else np.asarray(t_wc, np.float32), 1, f32(fx), f32(fy),
+                f32(width / 2.0 if cx is None else cx), f32(height / 2.0 if cy is None else cy))
+
+
+# camera -> world rotations of the six cube faces (camera axes: x right, y down, z forward)
+_CUBE_FACES = {
+    "+z": np.eye(3),
+    "-z": np.array([[-1.0, 0, 0], [0, 1, 0], [0, 0, -1]]),
+    "+x": np.array([[0.0, 0, 1], [0, 1, 0], [-1, 0, 0]]),
+    "-x": np.array([[0.0, 0, -1], [0, 1, 0], [1, 0, 0]]),
+    "+y": np.array([[1.0, 0, 0], [0, 0, 1], [0, -1, 0]]),
+    "-y": np.array([[1.0, 0, 0], [0, 0, -1], [0, 1, 0]]),
+}
+
+
+def cubemap_views(face, center=(0.0, 0.0, 0.0)):
+    """Six 90-degree pinhole views (face x face pixels) looking along +z, -z, +x, -x, +y, -y of the
+    world from ``center``: the 3DGS(P) cubemap rendering of a 360-degree scene."""
+    c = np.asarray(center, dtype=np.float64)
+    out = []
+    for name in ("+z", "-z", "+x", "-x", "+y", "-y"):
+        R_wc = _CUBE_FACES[name].T
+        out.append(pinhole_view(face, face, face / 2.0, face / 2.0, R_wc=R_wc, t_wc=-R_wc @ c))
+    return out
 
 
 def yaw_view(width, height, center, yaw) -> View:
