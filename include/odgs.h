@@ -55,13 +55,21 @@ typedef enum {
 
 #define ODGS_MAX_VIEWS 64
 
-/* One ERP camera. World point mu maps to camera space as t = R_wc mu + t_wc, with OpenCV
- * axes (x right, y down, z forward; Sec. 3.2). Pixel (i, j) is sampled at (i + 0.5, j + 0.5)
- * of the ERP plane of Eq. 4: u = W/(2 pi) phi + W/2, v = -H/pi theta + H/2. */
+/* One camera. World point mu maps to camera space as t = R_wc mu + t_wc, with OpenCV axes
+ * (x right, y down, z forward; Sec. 3.2). Pixel (i, j) is sampled at (i + 0.5, j + 0.5) of the
+ * image plane:
+ *   model 0 (ERP, the paper's camera): Eq. 4, u = W/(2 pi) phi + W/2, v = -H/pi theta + H/2;
+ *     culled inside the spherical shell r <= r_near or r >= r_far; depth key r = |t|; the
+ *     image wraps around the longitude seam.
+ *   model 1 (pinhole, the perspective case of Eq. 1, as in 3DGS(P) cube faces):
+ *     u = fx tx/tz + cx, v = fy ty/tz + cy; culled when tz <= r_near or tz >= r_far or when the
+ *     projected centre lies outside [-0.3 W, 1.3 W] x [-0.3 H, 1.3 H]; depth key tz; no wrap. */
 typedef struct {
-    int width, height; /* W must be a multiple of the tile width; any H >= 1   */
-    float R_wc[9];     /* row-major world -> camera rotation                    */
+    int width, height;     /* 1 <= W, H <= 16384; W a multiple of the tile width      */
+    float R_wc[9];         /* row-major world -> camera rotation                       */
     float t_wc[3];
+    int model;             /* 0: ERP, 1: pinhole                                       */
+    float fx, fy, cx, cy;  /* pinhole focal lengths (> 0) and principal point, pixels  */
 } odgs_view;
 
 typedef struct {

@@ -35,7 +35,8 @@ class OdgsError(RuntimeError):
 
 
 class View(C.Structure):
-    _fields_ = [("width", C.c_int), ("height", C.c_int), ("R_wc", C.c_float * 9), ("t_wc", C.c_float * 3)]
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("R_wc", C.c_float * 9), ("t_wc", C.c_float * 3),
+                ("model", C.c_int), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float)]
 
 
 class Settings(C.Structure):
@@ -153,11 +154,14 @@ def check(st: int, where: str):
         raise OdgsError(st, where)
 
 
-def make_view(width, height, R_wc, t_wc) -> View:
+def make_view(width, height, R_wc, t_wc, model=0, fx=0.0, fy=0.0, cx=0.0, cy=0.0) -> View:
+    """model 0: ERP; model 1: pinhole with focal lengths fx, fy and principal point cx, cy (pixels)."""
     v = View()
     v.width, v.height = int(width), int(height)
     v.R_wc[:] = [float(x) for x in list(_flat(R_wc))]
     v.t_wc[:] = [float(x) for x in list(_flat(t_wc))]
+    v.model = int(model)
+    v.fx, v.fy, v.cx, v.cy = float(fx), float(fy), float(cx), float(cy)
     return v
 
 

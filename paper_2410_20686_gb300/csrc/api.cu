@@ -112,28 +112,20 @@ odgs_status build_geometry(const odgs_view* views, int n_views, const odgs_setti
     long long tiles = 0, pixels = 0, trig = 0;
     for (int v = 0; v < n_views; ++v) {
         const odgs_view& w = views[v];
-        if (w.width < s.tile_w || w.height < 1 || w.width > 65535 || w.height > 65535) return ODGS_ERR_INVALID_ARG;
+        if (w.width < s.tile_w || w.height < 1 || w.width > 16384 || w.height > 16384) return ODGS_ERR_INVALID_ARG;
         if (w.width % s.tile_w != 0) return ODGS_ERR_INVALID_ARG;
         for (int i = 0; i < 9; ++i)
             if (!finite(w.R_wc[i])) return ODGS_ERR_INVALID_ARG;
         for (int i = 0; i < 3; ++i)
             if (!finite(w.t_wc[i])) return ODGS_ERR_INVALID_ARG;
         const int tx = w.width / s.tile_w, ty = (w.height + s.tile_h - 1) / s.tile_h;
-        if (tab) {
-            ViewDev& d = tab->v[v];
-            memset(&d, 0, sizeof(d));
-            d.W = w.width; d.H = w.height; d.tiles_x = tx; d.tiles_y = ty;
-            d.tile_base = (int)tiles; d.pix_base = (int)pixels;
-            d.trig_u = (int)trig; d.trig_v = (int)(trig + w.width);
-            for (int i = 0; i < 9; ++i) d.R[i] = w.R_wc[i];
-            for (int i = 0; i < 3; ++i) d.t[i] = w.t_wc[i];
-            // camera centre -R^T t (double accumulation, then rounded)
-            for (int j = 0; j < 3; ++j)
-                d.cam[j] = (float)-((double)w.R_wc[j] * w.t_wc[0] + (double)w.R_wc[3 + j] * w.t_wc[1] +
-                                    (double)w.R_wc[6 + j] * w.t_wc[2]);
-            d.fx = (float)((double)w.width / (2.0 * M_PI));
-            d.fy = (float)((double)w.height / M_PI);
-        }
+        ViewDev scratch_view{};
+        ViewDev& d = tab ? tab->v[v] : scratch_view;
+        memset(&d, 0, sizeof(d));
+        if (!fill_camera(w, d)) return ODGS_ERR_INVALID_ARG;
+        d.W = w.width; d.H = w.height; d.tiles_x = tx; d.tiles_y = ty;
+        d.tile_base = (int)tiles; d.pix_base = (int)pixels;
+        d.trig_u = (int)trig; d.trig_v = (int)(trig + w.width);
         tiles += (long long)tx * ty;
         pixels += (long long)w.width * w.height;
         trig += (long long)w.width + w.height;

@@ -149,7 +149,8 @@ __device__ __forceinline__ void emit_item_thread(uint32_t idx, uint4 rc, unsigne
     footprint_rows(fp, V.H, jlo, jhi);
     for (int ty = ty0 + 2; ty < ty0 + nb; ++ty) {
         int start, cnt;
-        band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, start, cnt);
+        band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, V.model == 0, start,
+                         cnt);
         const uint32_t row = (uint32_t)V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x;
         write_band(row, start, cnt, V.tiles_x, idx, off, a.capacity, 0, 1, a.keys, a.vals, s_hist, a.key_passes);
         off += (unsigned long long)cnt;
@@ -184,7 +185,8 @@ __device__ __forceinline__ void emit_item_warp(uint32_t idx, unsigned long long 
         const int ty = gq + lane;
         int start = 0, cnt = 0;
         if (ty <= ty1)
-            band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, start, cnt);
+            band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, V.model == 0, start,
+                         cnt);
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);

@@ -2,7 +2,8 @@
 //
 // Record layout per (view, Gaussian) item, written by the preprocess kernel and gathered by the
 // blend kernels (16-byte vector loads):
-//   rec_a = { du, dv, bits(c0 | r0 << 16), opacity }   ERP mean = (c0 + 0.5 + du, r0 + 0.5 + dv)
+//   rec_a = { du, dv, bits(c0 | r0 << 16), opacity }   mean = (c0 + 0.5 + du, r0 + 0.5 + dv)
+//   (c0, r0 as 16-bit two's complement: pinhole centres may lie left of or above the image)
 //   rec_b = { conic_a, conic_b, conic_c, 0 }            inverse of Sigma_2D (Eq. 8, dilated)
 //   rec_c = { r, g, b, 0 }                              SH colour
 // The mean is stored as an integer pixel anchor plus a small float offset so that the offset
@@ -37,9 +38,20 @@ struct ViewDev {
     float R[9];
     float t[3];
     float cam[3];   // camera centre in world space, -R^T t
-    float fx, fy;   // W / (2 pi), H / pi
-    float pad[3];
+    float fx, fy;   // ERP: W / (2 pi), H / pi; pinhole: the focal lengths in pixels
+    int model;      // 0: ERP (Eq. 4, periodic in u); 1: pinhole u = fx tx/tz + cx (Eq. 1)
+    float cx, cy;   // pinhole principal point
 };
+
+// Pixel anchor of a record: two signed 16-bit fields in the bits of a float.
+__device__ __forceinline__ float pack_anchor(int c0, int r0) {
+    return __uint_as_float(((uint32_t)c0 & 0xFFFFu) | ((uint32_t)r0 << 16));
+}
+__device__ __forceinline__ void unpack_anchor(float f, int& c0, int& r0) {
+    const uint32_t packed = __float_as_uint(f);
+    c0 = (int)(int16_t)(packed & 0xFFFFu);
+    r0 = (int)(int16_t)(packed >> 16);
+}
 
 // Device header at the start of the workspace.
 struct Header {
@@ -110,6 +122,12 @@ __device__ __forceinline__ ff ff_mulf(ff a, float b) {
     return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// a / b: a float quotient, then the quotient of the exact remainder
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = ff_add(a, ff_neg(ff_mulf(b, q1)));
+    return quick_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
 __device__ __forceinline__ ff ff_sqrt(ff a) {
     float s = __fsqrt_rn(a.hi);
     if (!(s > 0.f)) return {s, 0.f};
@@ -145,13 +163,13 @@ __device__ __forceinline__ int seam_shift(int i, int c0, float du, int W) {
     return 0;
 }
 
-__device__ __forceinline__ Staged stage_entry(float4 ra, float4 rb, float4 rc, int x0, int tw, int W) {
+// periodic: ERP views (seam-wrapped offsets); pinhole views have no seam.
+__device__ __forceinline__ Staged stage_entry(float4 ra, float4 rb, float4 rc, int x0, int tw, int W, bool periodic) {
     Staged s;
-    uint32_t packed = __float_as_uint(ra.z);
-    int c0 = (int)(packed & 0xFFFFu);
-    int r0 = (int)(packed >> 16);
-    int s0 = seam_shift(x0, c0, ra.x, W);
-    int s1 = seam_shift(x0 + tw - 1, c0, ra.x, W);
+    int c0, r0;
+    unpack_anchor(ra.z, c0, r0);
+    int s0 = periodic ? seam_shift(x0, c0, ra.x, W) : 0;
+    int s1 = periodic ? seam_shift(x0 + tw - 1, c0, ra.x, W) : 0;
     float fsplit = __int_as_float(0x7f800000);  // +inf
     float fc2 = (float)(c0 + s1);
     if (s0 != s1) {
@@ -201,9 +219,7 @@ struct Footprint {
 
 __device__ __forceinline__ Footprint make_footprint(float4 ra, float4 rb) {
     Footprint f;
-    uint32_t packed = __float_as_uint(ra.z);
-    f.c0 = (int)(packed & 0xFFFFu);
-    f.r0 = (int)(packed >> 16);
+    unpack_anchor(ra.z, f.c0, f.r0);
     f.du = ra.x;
     f.dv = ra.y;
     const float det = __fsub_rn(__fmul_rn(rb.x, rb.z), __fmul_rn(rb.y, rb.y));
@@ -234,9 +250,10 @@ __device__ __forceinline__ float slice_edge(const Footprint& f, float y, float s
 }
 
 // Tile columns of the band of pixel rows [J0, J1]: start column (mod tiles_x) and count (0 if
-// the slice holds no pixel centre).
+// the slice holds no pixel centre). periodic: ERP views wrap around the seam; pinhole views clip
+// the columns to the image.
 __device__ __forceinline__ void band_columns(const Footprint& f, int J0, int J1, int W, int tw, int tiles_x,
-                                             int& start, int& count) {
+                                             bool periodic, int& start, int& count) {
     const float d0 = fmaxf(__fsub_rn((float)(J0 - f.r0), f.dv), -f.ev);
     const float d1 = fminf(__fsub_rn((float)(J1 - f.r0), f.dv), f.ev);
     count = 0;
@@ -247,9 +264,17 @@ __device__ __forceinline__ void band_columns(const Footprint& f, int J0, int J1,
     const float xmax = __fadd_rn(slice_edge(f, yr, 1.f), 0.01f);
     const float xmin = __fsub_rn(slice_edge(f, yl, -1.f), 0.01f);
     const float half = (float)W;
-    if (!(xmax - xmin < half)) { start = 0; count = tiles_x; return; }
-    const int ilo = f.c0 + (int)ceilf(__fadd_rn(f.du, xmin));
-    const int ihi = f.c0 + (int)floorf(__fadd_rn(f.du, xmax));
+    int ilo, ihi;
+    if (periodic) {
+        if (!(xmax - xmin < half)) { start = 0; count = tiles_x; return; }
+        ilo = f.c0 + (int)ceilf(__fadd_rn(f.du, xmin));
+        ihi = f.c0 + (int)floorf(__fadd_rn(f.du, xmax));
+    } else {  // clamp before the conversion: a wide footprint can reach far outside the image
+        const float lo = fmaxf(__fadd_rn(f.du, xmin), (float)(-f.c0 - 1));
+        const float hi = fminf(__fadd_rn(f.du, xmax), (float)(W - f.c0));
+        ilo = max(f.c0 + (int)ceilf(lo), 0);
+        ihi = min(f.c0 + (int)floorf(hi), W - 1);
+    }
     if (ihi < ilo) return;
     if (ihi - ilo + 1 >= W) { start = 0; count = tiles_x; return; }
     const int tlo = floor_div_i(ilo, tw), thi = floor_div_i(ihi, tw);

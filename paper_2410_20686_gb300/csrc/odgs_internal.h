@@ -1,13 +1,37 @@
 // Launcher interfaces between the C-ABI host code (api.cu) and the kernel files.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "odgs.h"
 #include "odgs_common.cuh"
 
 namespace odgs {
+
+// Camera model fields of a ViewDev from the caller's view (false: invalid model or focal).
+inline bool fill_camera(const odgs_view& w, ViewDev& d) {
+    for (int i = 0; i < 9; ++i) d.R[i] = w.R_wc[i];
+    for (int i = 0; i < 3; ++i) d.t[i] = w.t_wc[i];
+    // camera centre -R^T t (double accumulation, then rounded)
+    for (int j = 0; j < 3; ++j)
+        d.cam[j] = (float)-((double)w.R_wc[j] * w.t_wc[0] + (double)w.R_wc[3 + j] * w.t_wc[1] +
+                            (double)w.R_wc[6 + j] * w.t_wc[2]);
+    d.model = w.model;
+    if (w.model == 0) {
+        d.fx = (float)((double)w.width / (2.0 * 3.14159265358979323846));
+        d.fy = (float)((double)w.height / 3.14159265358979323846);
+        d.cx = d.cy = 0.f;
+        return true;
+    }
+    if (w.model != 1) return false;
+    const bool fin = std::isfinite(w.fx) && std::isfinite(w.fy) && std::isfinite(w.cx) && std::isfinite(w.cy);
+    if (!fin || !(w.fx > 0.f) || !(w.fy > 0.f)) return false;
+    d.fx = w.fx; d.fy = w.fy; d.cx = w.cx; d.cy = w.cy;
+    return true;
+}
 
 struct ViewTable {
     ViewDev v[kMaxViews];

@@ -112,8 +112,9 @@ __device__ __forceinline__ void sh_grad_acc(float x, float y, float z, const flo
     }
 }
 
-// Radial depth in IEEE single precision with the fixed operation order of the depth key:
-// t_i = ((R_i0 m0 + R_i1 m1) + R_i2 m2) + t_i, r = sqrt((tx tx + ty ty) + tz tz).
+// Depth in IEEE single precision with the fixed operation order of the depth key:
+// t_i = ((R_i0 m0 + R_i1 m1) + R_i2 m2) + t_i; ERP: r = sqrt((tx tx + ty ty) + tz tz), the radial
+// distance; pinhole: tz, the z depth perspective 3DGS sorts by.
 __device__ __forceinline__ float depth_key(const ViewDev& V, float m0, float m1, float m2) {
     float t[3];
 #pragma unroll
@@ -122,6 +123,7 @@ __device__ __forceinline__ float depth_key(const ViewDev& V, float m0, float m1,
         s = __fadd_rn(s, __fmul_rn(V.R[3 * i + 2], m2));
         t[i] = __fadd_rn(s, V.t[i]);
     }
+    if (V.model == 1) return t[2];
     float q = __fadd_rn(__fmul_rn(t[0], t[0]), __fmul_rn(t[1], t[1]));
     q = __fadd_rn(q, __fmul_rn(t[2], t[2]));
     return __fsqrt_rn(q);
@@ -144,6 +146,13 @@ __device__ __forceinline__ JGeom omni_jacobian(float tx, float ty, float tz, flo
     g.J[0] = a * tz; g.J[1] = 0.f; g.J[2] = -a * tx;
     g.J[3] = -b * tx * ty; g.J[4] = fy * g.rho / g.r2; g.J[5] = -b * ty * tz;
     return g;
+}
+
+// Perspective Jacobian of u = fx tx/tz + cx, v = fy ty/tz + cy (Eq. 1).
+__device__ __forceinline__ void pinhole_jacobian(float tx, float ty, float tz, float fx, float fy, float J[6]) {
+    const float iz = 1.f / tz;
+    J[0] = fx * iz; J[1] = 0.f; J[2] = -fx * tx * iz * iz;
+    J[3] = 0.f; J[4] = fy * iz; J[5] = -fy * ty * iz * iz;
 }
 
 // TM = (J W) M, the 2x3 factor of Sigma_2D = TM TM^T (+ dilation).
@@ -250,36 +259,58 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                 t[i] = ff_add(acc, ff{V.t[i], 0.f});
             }
             const float tx = t[0].hi, ty = t[1].hi, tz = t[2].hi;
-            JGeom jg = omni_jacobian(tx, ty, tz, V.fx, V.fy);
-            ok = ok && (jg.rho > 1e-4f * r);  // too close to a pole: sec(theta) > 1e4
-            if (ok) {
+            float J[6];
+            float du = 0.f, dv = 0.f;
+            int c0 = 0, r0 = 0;
+            if (V.model == 1) {
+                // pinhole: u = fx tx/tz + cx (float-float), anchored at the pixel holding it;
+                // centres outside the image widened by 30 % on each side are culled
+                const ff uq = ff_add(ff{V.cx, 0.f}, ff_mulf(ff_div(t[0], t[2]), V.fx));
+                const ff vq = ff_add(ff{V.cy, 0.f}, ff_mulf(ff_div(t[1], t[2]), V.fy));
+                ok = ok && uq.hi >= -0.3f * V.W && uq.hi <= 1.3f * V.W && vq.hi >= -0.3f * V.H &&
+                     vq.hi <= 1.3f * V.H;
+                if (ok) {
+                    c0 = (int)floorf(uq.hi);
+                    r0 = (int)floorf(vq.hi);
+                    du = __fadd_rn(__fsub_rn(__fsub_rn(uq.hi, (float)c0), 0.5f), uq.lo);
+                    dv = __fadd_rn(__fsub_rn(__fsub_rn(vq.hi, (float)r0), 0.5f), vq.lo);
+                    pinhole_jacobian(tx, ty, tz, V.fx, V.fy, J);
+                }
+            } else {
+                JGeom jg = omni_jacobian(tx, ty, tz, V.fx, V.fy);
+                ok = ok && (jg.rho > 1e-4f * r);  // too close to a pole: sec(theta) > 1e4
+#pragma unroll
+                for (int i = 0; i < 6; ++i) J[i] = jg.J[i];
+            }
+            if (ok && V.model == 0) {
                 // ERP mean (Eq. 4) as pixel anchor + offset: rotate (t_x, t_z) by minus the
                 // azimuth of the anchor column's centre, then the elevation likewise.
                 float ua = atan2f(tx, tz) * V.fx + 0.5f * V.W;
-                int c0 = min(max((int)floorf(ua), 0), V.W - 1);
+                c0 = min(max((int)floorf(ua), 0), V.W - 1);
                 float4 tu = a.trig[V.trig_u + c0];
                 ff cph{tu.x, tu.y}, sph{tu.z, tu.w};
                 ff ar = ff_add(ff_mul(t[0], cph), ff_neg(ff_mul(t[2], sph)));  // rho sin(phi - phi0)
                 ff br = ff_add(ff_mul(t[0], sph), ff_mul(t[2], cph));          // rho cos(phi - phi0)
-                float du = atan2f(ar.hi, br.hi) * V.fx;
+                du = atan2f(ar.hi, br.hi) * V.fx;
                 ff rho = ff_sqrt(ff_add(ff_mul(ar, ar), ff_mul(br, br)));
                 ff ny = ff_neg(t[1]);
                 float va = -atan2f(ny.hi, rho.hi) * V.fy + 0.5f * V.H;
-                int r0 = min(max((int)floorf(va), 0), V.H - 1);
+                r0 = min(max((int)floorf(va), 0), V.H - 1);
                 float4 tv = a.trig[V.trig_v + r0];
                 ff cth{tv.x, tv.y}, sth{tv.z, tv.w};
                 ff ae = ff_add(ff_mul(ny, cth), ff_neg(ff_mul(rho, sth)));  // r sin(theta - theta0)
                 ff be = ff_add(ff_mul(rho, cth), ff_mul(ny, sth));          // r cos(theta - theta0)
-                float dv = -atan2f(ae.hi, be.hi) * V.fy;
-
+                dv = -atan2f(ae.hi, be.hi) * V.fy;
+            }
+            if (ok) {
                 // Sigma_2D = (J W M)(J W M)^T + delta I  (Eq. 8 and Sec. 3.1)
                 float T[6], TM[6];
-                tm_factor(jg.J, V.R, M, T, TM);
+                tm_factor(J, V.R, M, T, TM);
                 Cov2 c2 = cov2d(TM, a.st.dilation);
                 ok = c2.det > 0.f;
                 if (ok) {
                     float inv = 1.f / c2.det;
-                    const float4 ra = make_float4(du, dv, __uint_as_float((uint32_t)c0 | ((uint32_t)r0 << 16)), o);
+                    const float4 ra = make_float4(du, dv, pack_anchor(c0, r0), o);
                     const float4 rb = make_float4(c2.C * inv, -c2.B * inv, c2.A * inv, Qb);
                     // tiles met by the footprint, row band by row band (seam-wrapped columns)
                     Footprint fp = make_footprint(ra, rb);
@@ -292,7 +323,7 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                         for (int ty = ty0; ty <= ty1; ++ty) {
                             int st0, cnt;
                             band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.st.tile_w,
-                                         V.tiles_x, st0, cnt);
+                                         V.tiles_x, V.model == 0, st0, cnt);
                             count += (uint32_t)cnt;
                             if (ty - ty0 < 2) span[ty - ty0] = (uint32_t)st0 | ((uint32_t)cnt << 16);
                         }
@@ -440,9 +471,18 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) t[i] = W[3 * i] * m0 + W[3 * i + 1] * m1 + W[3 * i + 2] * m2 + V.t[i];
         const float tx = t[0], ty = t[1], tz = t[2];
-        JGeom jg = omni_jacobian(tx, ty, tz, V.fx, V.fy);
+        const bool pin = V.model == 1;
+        JGeom jg{};
+        float Jm[6];
+        if (pin) {
+            pinhole_jacobian(tx, ty, tz, V.fx, V.fy, Jm);
+        } else {
+            jg = omni_jacobian(tx, ty, tz, V.fx, V.fy);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) Jm[i] = jg.J[i];
+        }
         float T[6], TM[6];
-        tm_factor(jg.J, W, M, T, TM);
+        tm_factor(Jm, W, M, T, TM);
         Cov2 c2 = cov2d(TM, a.dilation);
         const float D = c2.det, iD2 = 1.f / (D * D);
         const float A = c2.A, B = c2.B, C = c2.C;
@@ -476,30 +516,40 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 dJ[3 * i + j] = dT[3 * i] * W[3 * j] + dT[3 * i + 1] * W[3 * j + 1] + dT[3 * i + 2] * W[3 * j + 2];
-        // dL/dt: mean path d(u, v)/dt = J_omni (Eq. 10) plus J_omni's dependence on t
+        // dL/dt: mean path d(u, v)/dt = J (Eq. 10 for ERP) plus J's dependence on t
         const float fx = V.fx, fy = V.fy;
-        const float rho = jg.rho, rho2 = jg.rho2, r2 = jg.r2;
-        const float irho4 = 1.f / (rho2 * rho2);
-        const float ir4 = 1.f / (r2 * r2);
-        const float irho = 1.f / rho, irho3 = irho / rho2;
-        float dtx = jg.J[0] * g0.x + jg.J[3] * g0.y;
-        float dty = jg.J[4] * g0.y;
-        float dtz = jg.J[2] * g0.x + jg.J[5] * g0.y;
-        // row 1: J11 = fx tz / rho^2, J13 = -fx tx / rho^2
-        dtx += fx * irho4 * (-2.f * tx * tz * dJ[0] + (tx * tx - tz * tz) * dJ[2]);
-        dtz += fx * irho4 * ((tx * tx - tz * tz) * dJ[0] + 2.f * tx * tz * dJ[2]);
-        // row 2: J21 = -fy tx ty / (r^2 rho), J22 = fy rho / r^2, J23 = -fy ty tz / (r^2 rho)
-        const float k3 = fy * ir4 * irho3, k1 = fy * ir4 * irho;
-        const float rr = 2.f * rho2 + r2;
-        dtx += -k3 * ty * (tz * tz * r2 - 2.f * tx * tx * rho2) * dJ[3];
-        dty += -k1 * tx * (r2 - 2.f * ty * ty) * dJ[3];
-        dtz += k3 * tx * ty * tz * rr * dJ[3];
-        dtx += k1 * tx * (r2 - 2.f * rho2) * dJ[4];
-        dty += -2.f * fy * ir4 * rho * ty * dJ[4];
-        dtz += k1 * tz * (r2 - 2.f * rho2) * dJ[4];
-        dtx += k3 * tx * ty * tz * rr * dJ[5];
-        dty += -k1 * tz * (r2 - 2.f * ty * ty) * dJ[5];
-        dtz += -k3 * ty * (tx * tx * r2 - 2.f * tz * tz * rho2) * dJ[5];
+        float dtx, dty, dtz;
+        if (pin) {
+            // J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]] (Eq. 1)
+            const float iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+            dtx = Jm[0] * g0.x - dJ[2] * fx * iz2;
+            dty = Jm[4] * g0.y - dJ[5] * fy * iz2;
+            dtz = Jm[2] * g0.x + Jm[5] * g0.y - dJ[0] * fx * iz2 + 2.f * dJ[2] * fx * tx * iz3 - dJ[4] * fy * iz2 +
+                  2.f * dJ[5] * fy * ty * iz3;
+        } else {
+            const float rho = jg.rho, rho2 = jg.rho2, r2 = jg.r2;
+            const float irho4 = 1.f / (rho2 * rho2);
+            const float ir4 = 1.f / (r2 * r2);
+            const float irho = 1.f / rho, irho3 = irho / rho2;
+            dtx = jg.J[0] * g0.x + jg.J[3] * g0.y;
+            dty = jg.J[4] * g0.y;
+            dtz = jg.J[2] * g0.x + jg.J[5] * g0.y;
+            // row 1: J11 = fx tz / rho^2, J13 = -fx tx / rho^2
+            dtx += fx * irho4 * (-2.f * tx * tz * dJ[0] + (tx * tx - tz * tz) * dJ[2]);
+            dtz += fx * irho4 * ((tx * tx - tz * tz) * dJ[0] + 2.f * tx * tz * dJ[2]);
+            // row 2: J21 = -fy tx ty / (r^2 rho), J22 = fy rho / r^2, J23 = -fy ty tz / (r^2 rho)
+            const float k3 = fy * ir4 * irho3, k1 = fy * ir4 * irho;
+            const float rr = 2.f * rho2 + r2;
+            dtx += -k3 * ty * (tz * tz * r2 - 2.f * tx * tx * rho2) * dJ[3];
+            dty += -k1 * tx * (r2 - 2.f * ty * ty) * dJ[3];
+            dtz += k3 * tx * ty * tz * rr * dJ[3];
+            dtx += k1 * tx * (r2 - 2.f * rho2) * dJ[4];
+            dty += -2.f * fy * ir4 * rho * ty * dJ[4];
+            dtz += k1 * tz * (r2 - 2.f * rho2) * dJ[4];
+            dtx += k3 * tx * ty * tz * rr * dJ[5];
+            dty += -k1 * tz * (r2 - 2.f * ty * ty) * dJ[5];
+            dtz += -k3 * ty * (tx * tx * r2 - 2.f * tz * tz * rho2) * dJ[5];
+        }
         // t = W mu + t_wc
         gm[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
         gm[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                 const uint32_t idx = a.pair_vals[rg.x + lo + j];
                 float4 ra, rb, rc;
                 gather_records(a.rec_a, a.rec_b, a.rec_c, idx, a.n_items, ra, rb, rc);
-                Staged s = stage_entry(ra, rb, rc, x0, tw, V.W);
+                Staged s = stage_entry(ra, rb, rc, x0, tw, V.W, V.model == 0);
                 s_pos[j] = s.pos;
                 s_con[j] = s.con;
                 s_col[j] = s.col;

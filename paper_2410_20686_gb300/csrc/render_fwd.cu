@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
                 const uint32_t idx = a.pair_vals[rg.x + b0 + j];
                 float4 ra, rb, rc;
                 gather_records(a.rec_a, a.rec_b, a.rec_c, idx, a.n_items, ra, rb, rc);
-                Staged s = stage_entry(ra, rb, rc, x0, tw, V.W);
+                Staged s = stage_entry(ra, rb, rc, x0, tw, V.W, V.model == 0);
                 s_pos[j] = s.pos;
                 s_con[j] = s.con;
                 s_col[j] = s.col;

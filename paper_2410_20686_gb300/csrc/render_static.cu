@@ -60,6 +60,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     if (!g || !view || !s || !image || !status_out) return ODGS_ERR_INVALID_ARG;
     if (g->n < 0 || g->n > kStaticMaxGaussians) return ODGS_ERR_INVALID_ARG;
     if ((long long)view->width * view->height > kStaticMaxPixels) return ODGS_ERR_INVALID_ARG;
+    if (view->width > 16384 || view->height > 16384) return ODGS_ERR_INVALID_ARG;
     if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh)) return ODGS_ERR_INVALID_ARG;
     if (g->n > 0 && reinterpret_cast<uintptr_t>(g->quats) % 16 != 0) return ODGS_ERR_INVALID_ARG;
     odgs_settings st = *s;
@@ -96,13 +97,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     V.tiles_x = W / st.tile_w;
     V.tiles_y = (H + st.tile_h - 1) / st.tile_h;
     V.tile_base = 0; V.pix_base = 0; V.trig_u = 0; V.trig_v = W;
-    for (int i = 0; i < 9; ++i) V.R[i] = view->R_wc[i];
-    for (int i = 0; i < 3; ++i) V.t[i] = view->t_wc[i];
-    for (int j = 0; j < 3; ++j)
-        V.cam[j] = (float)-((double)view->R_wc[j] * view->t_wc[0] + (double)view->R_wc[3 + j] * view->t_wc[1] +
-                            (double)view->R_wc[6 + j] * view->t_wc[2]);
-    V.fx = (float)((double)W / (2.0 * 3.14159265358979323846));
-    V.fy = (float)((double)H / 3.14159265358979323846);
+    if (!fill_camera(*view, V)) return ODGS_ERR_INVALID_ARG;
     tab.n_views = 1;
     tab.n_items = (uint32_t)g->n;
     const int tiles = V.tiles_x * V.tiles_y;

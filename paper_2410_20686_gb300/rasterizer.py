@@ -52,7 +52,8 @@ def _views_array(views):
         if isinstance(v, L.View):
             arr[i] = v
         else:
-            arr[i] = L.make_view(v.width, v.height, v.R_wc, v.t_wc)
+            arr[i] = L.make_view(v.width, v.height, v.R_wc, v.t_wc, getattr(v, "model", 0), getattr(v, "fx", 0.0),
+                                 getattr(v, "fy", 0.0), getattr(v, "cx", 0.0), getattr(v, "cy", 0.0))
     return arr
 
 
