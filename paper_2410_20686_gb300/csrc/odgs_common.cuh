@@ -290,6 +290,15 @@ __device__ __forceinline__ void pixel_offset(float fi, float fj, float fc, float
     dy = __fsub_rn(__fsub_rn(fj, pos.y), pos.w);
 }
 
+// 2^p by the hardware's base-2 exponential (PTX ex2.approx.ftz.f32: relative error below 2^-22;
+// the blend evaluates it only for p >= log2(1/255), so no result is subnormal). Forward and
+// backward both use it, so they compute the same alpha.
+__device__ __forceinline__ float alpha_exp2(float p) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+    return r;
+}
+
 // Base-2 exponent of alpha before the clamp: log2(o) - 0.5 log2(e) d^T conic d (Eq. 2).
 __device__ __forceinline__ float gauss_exponent(float4 con, float dx, float dy) {
     float q = __fmaf_rn(con.x, dx, __fmul_rn(con.y, dy));

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                         for (int k = 0; k < PPT; ++k) {
                             if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
                             const float dx = dxk[k];
-                            const float ar = exp2f(pk[k]);
+                            const float ar = alpha_exp2(pk[k]);
                             const float alpha = fminf(kAlphaMax, ar);
                             const float inv = __fdividef(1.f, __fsub_rn(1.f, alpha));
                             const float Tj = T[k] * inv;

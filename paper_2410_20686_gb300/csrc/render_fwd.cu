@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (done[k] || pk[k] < kLog2AlphaMin) continue;
-                    const float alpha = fminf(kAlphaMax, exp2f(pk[k]));
+                    const float alpha = fminf(kAlphaMax, alpha_exp2(pk[k]));
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     if (Tn < kTMin) {
                         done[k] = true;
