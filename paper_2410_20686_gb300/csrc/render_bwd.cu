@@ -183,6 +183,10 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                         contrib = true;
                         const float4 c = s_col[j];
                         const float4 R = s_raw[j];
+                        // sums over this thread's pixels of dp, dp dx and dp dx^2 (dp = dL/d power);
+                        // the conic, opacity and mean terms follow from them once per entry, as dy
+                        // is the same for all of the thread's pixels
+                        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
@@ -199,16 +203,21 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                             const float dLda = Tj * cg - Bg[k] * inv;
                             Bg[k] = fmaf(cg, w, Bg[k]);
                             T[k] = Tj;
-                            if (ar < kAlphaMax) {
+                            if (ar < kAlphaMax) {  // no gradient through the 0.99 clamp
                                 const float dp = dLda * alpha;  // dL/d(power), power = ln G
-                                vals[5] += dp * R.w;
-                                vals[2] += dp * (-0.5f * dx * dx);
-                                vals[3] += dp * (-dx * dy);
-                                vals[4] += dp * (-0.5f * dy * dy);
-                                vals[0] += dp * (R.x * dx + R.y * dy);
-                                vals[1] += dp * (R.y * dx + R.z * dy);
+                                const float dpx = dp * dx;
+                                S0 += dp;
+                                S1 += dpx;
+                                S2 = fmaf(dpx, dx, S2);
                             }
                         }
+                        // power = ln o - (a dx^2 + 2 b dx dy + c dy^2) / 2 with (dx, dy) = pixel - mean
+                        vals[5] = S0 * R.w;
+                        vals[2] = -0.5f * S2;
+                        vals[3] = -dy * S1;
+                        vals[4] = (-0.5f * dy * dy) * S0;
+                        vals[0] = R.x * S1 + (R.y * dy) * S0;
+                        vals[1] = R.y * S1 + (R.z * dy) * S0;
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, contrib);
