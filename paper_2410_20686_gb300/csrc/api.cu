@@ -17,7 +17,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t hdr, views, trig, rec_a, rec_b, rec_c, rect, dkey0, dkey1, dval0, dval1, block_sums, ranges, T_final,
+    size_t hdr, views, trig, rec_a, rec_b, rec_c, rect, rect2, dkey0, dkey1, dval0, dval1, block_sums, ranges, T_final,
         n_last, acc, sort_hist, sort_ctr, sort_lb, big, total;
 };
 
@@ -45,6 +45,7 @@ Layout make_layout(size_t items, const Geometry& g) {
     L.rec_b = take(sizeof(float4) * items);
     L.rec_c = take(sizeof(float4) * items);
     L.rect = take(sizeof(uint4) * items);
+    L.rect2 = take(sizeof(uint4) * items);
     L.dkey0 = take(sizeof(uint32_t) * items);
     L.dkey1 = take(sizeof(uint32_t) * items);
     L.dval0 = take(sizeof(uint32_t) * items);
@@ -237,6 +238,7 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.rec_b = reinterpret_cast<float4*>(w + c->L.rec_b);
     a.rec_c = reinterpret_cast<float4*>(w + c->L.rec_c);
     a.rect = reinterpret_cast<uint4*>(w + c->L.rect);
+    a.rect2 = reinterpret_cast<uint4*>(w + c->L.rect2);
     a.dkey = reinterpret_cast<uint32_t*>(w + c->L.dkey0);
     a.dval = reinterpret_cast<uint32_t*>(w + c->L.dval0);
     a.hdr = hdr;
@@ -330,6 +332,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     BinArgs b{};
     b.sorted_idx = dv[rb];
     b.rect = reinterpret_cast<const uint4*>(w + c->L.rect);
+    b.rect2 = reinterpret_cast<const uint4*>(w + c->L.rect2);
     b.rec_a = reinterpret_cast<const float4*>(w + c->L.rec_a);
     b.rec_b = reinterpret_cast<const float4*>(w + c->L.rec_b);
     b.tile_w = c->s.tile_w;

@@ -128,26 +128,43 @@ __device__ __forceinline__ void write_band(uint32_t row, int start, int cnt, int
     count_run(row, cnt - first, s_hist, passes, lane0, nlanes);
 }
 
-// Emits all pairs of one item from offset off, by one thread. The spans of the item's first two
-// row bands were stored by the preprocess; further bands are recomputed (same functions).
+// Spans of the item's first kStoredBands row bands, as the preprocess stored them.
+constexpr int kStoredBands = 6;
+__device__ __forceinline__ void stored_spans(uint32_t idx, uint4 rc, const EmitArgs& a, uint32_t spans[kStoredBands]) {
+    spans[0] = rc.z;
+    spans[1] = rc.w;
+    if ((rc.x >> 16) > 2u) {
+        const uint4 r2 = a.rect2[idx];
+        spans[2] = r2.x; spans[3] = r2.y; spans[4] = r2.z; spans[5] = r2.w;
+    } else {
+        spans[2] = spans[3] = spans[4] = spans[5] = 0u;
+    }
+}
+
+// Emits all pairs of one item from offset off, by one thread. The spans of the item's first
+// kStoredBands row bands were stored by the preprocess; further bands are recomputed (same
+// functions).
 __device__ __forceinline__ void emit_item_thread(uint32_t idx, uint4 rc, unsigned long long off, const EmitArgs& a,
                                                  uint32_t (*s_hist)[256]) {
     const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
     const int ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
     const int th = a.tile_h;
-    const uint32_t spans[2] = {rc.z, rc.w};
-    for (int b = 0; b < nb && b < 2; ++b) {
+    uint32_t spans[kStoredBands];
+    stored_spans(idx, rc, a, spans);
+#pragma unroll
+    for (int b = 0; b < kStoredBands; ++b) {  // constant indices: the spans stay in registers
+        if (b >= nb) break;
         const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
         const int cnt = (int)(spans[b] >> 16);
         write_band(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, off, a.capacity, 0, 1, a.keys, a.vals,
                    s_hist, a.key_passes);
         off += (unsigned long long)cnt;
     }
-    if (nb <= 2) return;
+    if (nb <= kStoredBands) return;
     Footprint fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
     int jlo, jhi;
     footprint_rows(fp, V.H, jlo, jhi);
-    for (int ty = ty0 + 2; ty < ty0 + nb; ++ty) {
+    for (int ty = ty0 + kStoredBands; ty < ty0 + nb; ++ty) {
         int start, cnt;
         band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, V.model == 0, start,
                          cnt);
@@ -164,10 +181,13 @@ __device__ __forceinline__ void emit_item_warp(uint32_t idx, unsigned long long 
     const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
     const uint4 rc = a.rect[idx];
     const int th = a.tile_h;
-    if ((rc.x >> 16) <= 2u) {  // spans stored by the preprocess
+    if ((rc.x >> 16) <= (uint32_t)kStoredBands) {  // spans stored by the preprocess
         const int ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
-        const uint32_t spans[2] = {rc.z, rc.w};
-        for (int b = 0; b < nb; ++b) {
+        uint32_t spans[kStoredBands];
+        stored_spans(idx, rc, a, spans);
+#pragma unroll
+        for (int b = 0; b < kStoredBands; ++b) {
+            if (b >= nb) break;
             const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
             const int cnt = (int)(spans[b] >> 16);
             write_band(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, off, a.capacity, lane, 32, a.keys, a.vals,
@@ -328,7 +348,7 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
     if (nb == 0 && (e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
     if (nb > 0) {
         EmitArgs ea{};
-        ea.sorted_idx = a.sorted_idx; ea.rect = a.rect; ea.rec_a = a.rec_a; ea.rec_b = a.rec_b; ea.views = a.views;
+        ea.sorted_idx = a.sorted_idx; ea.rect = a.rect; ea.rect2 = a.rect2; ea.rec_a = a.rec_a; ea.rec_b = a.rec_b; ea.views = a.views;
         ea.n_per_view = a.n_per_view; ea.n_items = a.n_items; ea.tile_w = a.tile_w; ea.tile_h = a.tile_h;
         ea.block_offsets = a.block_sums; ea.capacity = a.capacity; ea.keys = a.keys; ea.vals = a.vals;
         ea.big = a.big; ea.hdr = a.hdr;

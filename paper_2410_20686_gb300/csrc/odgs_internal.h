@@ -46,7 +46,8 @@ struct PreArgs {
     const float4* trig;
     Settings st;
     float4 *rec_a, *rec_b, *rec_c;
-    uint4* rect;  // (ty0 | bands << 16, tiles, span of band 0, span of band 1); span = start | count << 16
+    uint4* rect;   // (ty0 | bands << 16, tiles, span of band 0, span of band 1); span = start | count << 16
+    uint4* rect2;  // spans of bands 2..5 (items with more than 2 bands)
     uint32_t *dkey, *dval;
     Header* hdr;
 };
@@ -68,6 +69,7 @@ struct PreBwdArgs {
 struct BinArgs {
     const uint32_t* sorted_idx;
     const uint4* rect;
+    const uint4* rect2;
     const float4 *rec_a, *rec_b;
     int tile_w, tile_h;
     const ViewDev* views;
@@ -86,6 +88,7 @@ struct BinArgs {
 struct EmitArgs {
     const uint32_t* sorted_idx;
     const uint4* rect;
+    const uint4* rect2;
     const float4 *rec_a, *rec_b;
     const ViewDev* views;
     int n_per_view;

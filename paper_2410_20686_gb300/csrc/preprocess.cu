@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                     Footprint fp = make_footprint(ra, rb);
                     int jlo, jhi;
                     footprint_rows(fp, V.H, jlo, jhi);
-                    uint32_t count = 0u, span[2] = {0u, 0u};
+                    uint32_t count = 0u, sp0 = 0u, sp1 = 0u, sp2 = 0u, sp3 = 0u, sp4 = 0u, sp5 = 0u;
                     const int th = a.st.tile_h;
                     const int ty0 = jlo / th, ty1 = jhi / th;
                     if (jlo <= jhi) {
@@ -325,11 +325,16 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                             band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.st.tile_w,
                                          V.tiles_x, V.model == 0, st0, cnt);
                             count += (uint32_t)cnt;
-                            if (ty - ty0 < 2) span[ty - ty0] = (uint32_t)st0 | ((uint32_t)cnt << 16);
+                            // spans of the first six bands (scalars, so that they stay in registers)
+                            const uint32_t sp = (uint32_t)st0 | ((uint32_t)cnt << 16);
+                            const int b = ty - ty0;
+                            sp0 = b == 0 ? sp : sp0; sp1 = b == 1 ? sp : sp1; sp2 = b == 2 ? sp : sp2;
+                            sp3 = b == 3 ? sp : sp3; sp4 = b == 4 ? sp : sp4; sp5 = b == 5 ? sp : sp5;
                         }
                     }
                     if (count > 0u) {
-                        rect = make_uint4((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count, span[0], span[1]);
+                        rect = make_uint4((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count, sp0, sp1);
+                        if (ty1 - ty0 >= 2) a.rect2[item] = make_uint4(sp2, sp3, sp4, sp5);
                         local_pairs += count;
                         ++local_visible;
                         key = __float_as_uint(r);

@@ -119,6 +119,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     float4* rec_b = reinterpret_cast<float4*>(take(sizeof(float4) * n));
     float4* rec_c = reinterpret_cast<float4*>(take(sizeof(float4) * n));
     uint4* rect = reinterpret_cast<uint4*>(take(sizeof(uint4) * n));
+    uint4* rect2 = reinterpret_cast<uint4*>(take(sizeof(uint4) * n));
     uint32_t* dk[2] = {reinterpret_cast<uint32_t*>(take(4 * n)), reinterpret_cast<uint32_t*>(take(4 * n))};
     uint32_t* dv[2] = {reinterpret_cast<uint32_t*>(take(4 * n)), reinterpret_cast<uint32_t*>(take(4 * n))};
     unsigned long long* block_sums =
@@ -155,7 +156,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     a.st.dilation = st.cov_dilation; a.st.r_near = st.r_near; a.st.r_far = st.r_far;
     for (int i = 0; i < 3; ++i) a.st.bg[i] = st.bg[i];
     a.st.raw = st.raw_params;
-    a.rec_a = rec_a; a.rec_b = rec_b; a.rec_c = rec_c; a.rect = rect; a.dkey = dk[0]; a.dval = dv[0];
+    a.rec_a = rec_a; a.rec_b = rec_b; a.rec_c = rec_c; a.rect = rect; a.rect2 = rect2; a.dkey = dk[0]; a.dval = dv[0];
     a.hdr = hdr;
     if (launch_preprocess(a, st.sh_degree, strm) != cudaSuccess) return ODGS_ERR_CUDA;
     int rb = 0;
@@ -163,7 +164,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
                           &launches) != cudaSuccess)
         return ODGS_ERR_CUDA;
     BinArgs b{};
-    b.sorted_idx = dv[rb]; b.rect = rect; b.views = vd; b.n_per_view = g->n > 0 ? g->n : 1;
+    b.sorted_idx = dv[rb]; b.rect = rect; b.rect2 = rect2; b.views = vd; b.n_per_view = g->n > 0 ? g->n : 1;
     b.rec_a = rec_a; b.rec_b = rec_b; b.tile_w = st.tile_w; b.tile_h = st.tile_h;
     b.n_items = (uint32_t)n; b.block_sums = block_sums; b.hdr = hdr; b.capacity = cap;
     b.keys = pk[0]; b.vals = pv[0];
