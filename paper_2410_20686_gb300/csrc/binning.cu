@@ -16,7 +16,7 @@
 namespace odgs {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 __device__ __forceinline__ uint32_t rect_tiles(uint4 r) { return r.y; }
@@ -89,6 +89,21 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __rest
 // shared histogram. Lanes [lane0, lane0 + nlanes) share the low digit (distinct bins, one atomic
 // per key); the first lane adds the higher digits one constant-digit segment at a time, so a row
 // of consecutive tiles costs one atomic per higher digit instead of one per key.
+// Higher digits (passes 1 and up) of the run of consecutive keys key0 .. key0 + cnt - 1.
+__device__ __forceinline__ void count_high(uint32_t key0, int cnt, uint32_t (*s_hist)[256], int passes) {
+    if (cnt <= 0) return;
+    const uint32_t end = key0 + (uint32_t)cnt;
+    for (int p = 1; p < passes; ++p) {
+        const int sh = 8 * p;
+        uint32_t k = key0;
+        while (k < end) {
+            const uint32_t seg_end = min(end, ((k >> sh) + 1u) << sh);
+            atomicAdd(&s_hist[p][(k >> sh) & 0xFFu], seg_end - k);
+            k = seg_end;
+        }
+    }
+}
+
 __device__ __forceinline__ void count_run(uint32_t key0, int cnt, uint32_t (*s_hist)[256], int passes, int lane0,
                                           int nlanes) {
     if (cnt <= 0) return;
@@ -185,14 +200,46 @@ __device__ __forceinline__ void emit_item_warp(uint32_t idx, unsigned long long 
         const int ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
         uint32_t spans[kStoredBands];
         stored_spans(idx, rc, a, spans);
+        // the item's pairs as one range: pair t lies in the band b with cum[b] <= t < cum[b + 1]
+        int cum[kStoredBands + 1];
+        cum[0] = 0;
 #pragma unroll
-        for (int b = 0; b < kStoredBands; ++b) {
-            if (b >= nb) break;
-            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
-            const int cnt = (int)(spans[b] >> 16);
-            write_band(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, off, a.capacity, lane, 32, a.keys, a.vals,
-                       s_hist, a.key_passes);
-            off += (unsigned long long)cnt;
+        for (int b = 0; b < kStoredBands; ++b) cum[b + 1] = cum[b] + (b < nb ? (int)(spans[b] >> 16) : 0);
+        if (off >= a.capacity) return;  // pairs beyond the capacity are neither written nor counted
+        const int avail = (int)min((unsigned long long)cum[kStoredBands], a.capacity - off);
+        const int tiles_x = V.tiles_x;
+        for (int t = lane; t < avail; t += 32) {
+            int b = 0;
+#pragma unroll
+            for (int q = 1; q < kStoredBands; ++q) b += t >= cum[q] ? 1 : 0;
+            uint32_t sp = spans[0];
+            int c0 = 0;
+#pragma unroll
+            for (int q = 1; q < kStoredBands; ++q) {  // selects: the arrays stay in registers
+                sp = b == q ? spans[q] : sp;
+                c0 = b == q ? cum[q] : c0;
+            }
+            int col = (int)(sp & 0xFFFFu) + (t - c0);
+            if (col >= tiles_x) col -= tiles_x;
+            const uint32_t key = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)tiles_x + (uint32_t)col;
+            a.keys[off + (unsigned long long)t] = key;
+            a.vals[off + (unsigned long long)t] = idx;
+            atomicAdd(&s_hist[0][key & 0xFFu], 1u);
+        }
+        if (a.key_passes > 1 && lane < nb) {  // higher digits: lane b counts the runs of band b
+            uint32_t sp = spans[0];
+            int c0 = 0;
+#pragma unroll
+            for (int q = 1; q < kStoredBands; ++q) {
+                sp = lane == q ? spans[q] : sp;
+                c0 = lane == q ? cum[q] : c0;
+            }
+            const int c = min(max(avail - c0, 0), (int)(sp >> 16));
+            const int start = (int)(sp & 0xFFFFu);
+            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + lane) * (uint32_t)tiles_x;
+            const int first = min(c, tiles_x - start);
+            count_high(row + (uint32_t)start, first, s_hist, a.key_passes);
+            count_high(row, c - first, s_hist, a.key_passes);
         }
         return;
     }
