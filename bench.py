@@ -485,6 +485,7 @@ def run_ours(args):
 
     from paper_2410_20686_gb300 import build as B
     from paper_2410_20686_gb300 import scenes as S
+    from paper_2410_20686_gb300.loss import l1_dssim
     from paper_2410_20686_gb300.rasterizer import Rasterizer, RenderSettings
 
     world, rank, local = dist_env()
@@ -522,9 +523,9 @@ def run_ours(args):
         imgs, _ = rast.render_fwd(want_T=False)
         if record is not None:
             record[3].record()
-        diff = imgs[0] - target
-        loss = diff.abs().mean()
-        g = torch.sign(diff) * (1.0 / diff.numel())  # dL/dC of the mean absolute error
+        # mean absolute error and its gradient sign(C - target) / (3 W H), one fused kernel
+        loss, gl = l1_dssim([imgs[0]], [target], lam=0.0, area_weight=False)
+        g = gl[0]
         if record is not None:
             record[4].record()
         rast.render_bwd([g])

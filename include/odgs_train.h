@@ -116,6 +116,7 @@ odgs_status odgs_adam_step(const odgs_adam_group *groups, int n_groups, const od
  * cos(theta_j) when area_weight = 1 (theta_j = pi (1/2 - (j + 1/2) / H), Eq. 4's elevation of
  * the row centre: the solid angle of the row). The window wraps around the longitude seam when
  * wrap_u = 1 (zero padding otherwise) and is zero-padded above and below the image.
+ * With lambda = 0 the call computes the (weighted) L1 term alone in one pass over the pixels.
  * image, target: device [3][H][W] float32. grad: device [3][H][W], receives dL/dimage (the L1
  * term's derivative at image == target is 0); may be NULL. loss: device float, receives L (or L
  * is added to it when accumulate = 1, so that views sum into one value). scratch:

@@ -16,7 +16,7 @@
 namespace odgs {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 4;
+constexpr int kScanItems = 2;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 __device__ __forceinline__ uint32_t rect_tiles(uint4 r) { return r.y; }

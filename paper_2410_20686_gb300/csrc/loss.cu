@@ -180,6 +180,25 @@ __global__ void __launch_bounds__(kThreads) k_ssim_bwd(LossArgs a) {
     }
 }
 
+// lambda = 0: the weighted L1 term alone, one pass over the pixels (no window): the loss partial
+// of each CTA and the gradient w sign(x - y) / (weight sum).
+__global__ void __launch_bounds__(kThreads) k_l1(LossArgs a) {
+    __shared__ float s_red[kThreads / 32];
+    float part = 0.f;
+    for (int rc = blockIdx.x; rc < 3 * a.H; rc += gridDim.x) {  // (channel, row) pairs
+        const int row = rc % a.H;
+        const float w = row_weight(a, row) * a.inv_wsum;
+        const size_t base = (size_t)rc * a.W;
+        for (int col = threadIdx.x; col < a.W; col += kThreads) {
+            const float d = a.x[base + col] - a.y[base + col];
+            part = fmaf(w, fabsf(d), part);
+            if (a.grad) a.grad[base + col] = d > 0.f ? w : (d < 0.f ? -w : 0.f);
+        }
+    }
+    const float t = block_sum(part, s_red);
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = t;
+}
+
 __global__ void __launch_bounds__(kThreads) k_loss_reduce(const float* __restrict__ partial, int n, float* loss,
                                                           int accumulate) {
     __shared__ float s_red[kThreads / 32];
@@ -229,6 +248,12 @@ extern "C" odgs_status odgs_loss_l1_dssim(const float* image, const float* targe
     }
     for (int k = 0; k < kWin; ++k) a.g[k] = (float)(g[k] / gsum);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->lambda == 0.f) {  // L1 alone: no SSIM window
+        const int blocks = min(blocks_for(width, height), 3 * height);
+        k_l1<<<blocks, kThreads, 0, st>>>(a);
+        k_loss_reduce<<<1, kThreads, 0, st>>>(a.partial, blocks, loss, p->accumulate ? 1 : 0);
+        return cudaGetLastError() == cudaSuccess ? ODGS_OK : ODGS_ERR_CUDA;
+    }
     const dim3 grid((width + kTX - 1) / kTX, (height + kTY - 1) / kTY);
     k_ssim_fwd<<<grid, kThreads, 0, st>>>(a);
     k_loss_reduce<<<1, kThreads, 0, st>>>(a.partial, blocks_for(width, height), loss, p->accumulate ? 1 : 0);

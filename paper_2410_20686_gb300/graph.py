@@ -20,15 +20,10 @@ _GRAD_NAMES = ("means", "scales", "quats", "opacity", "sh")
 
 
 def l1_grad(images, targets):
-    """Gradient of sum_v mean |I_v - T_v| w.r.t. each image (and the loss itself)."""
-    loss = None
-    grads = []
-    for im, tg in zip(images, targets):
-        d = im - tg
-        lv = d.abs().mean()
-        loss = lv if loss is None else loss + lv
-        grads.append(torch.sign(d) * (1.0 / d.numel()))
-    return loss, grads
+    """sum_v mean |I_v - T_v| and its gradient w.r.t. each image, sign(I - T) / (3 W H), by the
+    fused loss kernel (L1 term alone, unweighted)."""
+    from .loss import l1_dssim
+    return l1_dssim(images, targets, lam=0.0, area_weight=False, wrap_u=True)
 
 
 class GraphedFrame:

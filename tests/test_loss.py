@@ -29,6 +29,19 @@ def test_loss_and_gradient_match_the_oracle(W, H, area, wrap):
     np.testing.assert_allclose(g, ref_grad, rtol=0, atol=1e-4 * np.abs(ref_grad).max())
 
 
+@pytest.mark.parametrize("W,H,area", [(256, 128, True), (200, 50, False), (2048, 1024, False)])
+def test_l1_alone_matches_the_oracle(W, H, area):
+    import torch
+    from paper_2410_20686_gb300.loss import l1_dssim
+    x, y = _pair(W, H, 3 * W + H)
+    loss, grads = l1_dssim([torch.from_numpy(x).cuda()], [torch.from_numpy(y).cuda()], lam=0.0, area_weight=area)
+    ref_loss, ref_grad = OL.loss_and_grad(x, y, lam=0.0, area_weight=area)
+    assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+    np.testing.assert_allclose(grads[0].cpu().numpy(), ref_grad, rtol=1e-5, atol=1e-5 * np.abs(ref_grad).max())
+    if not area:  # the plain mean absolute error: gradient sign(x - y) / (3 W H)
+        np.testing.assert_array_equal(grads[0].cpu().numpy() != 0, x != y)
+
+
 def test_identical_images_give_zero_loss_and_gradient():
     import torch
     from paper_2410_20686_gb300.loss import l1_dssim
