@@ -419,9 +419,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
 
     float gm[3] = {0.f, 0.f, 0.f}, gop = 0.f;
-    float gsh[16][3];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
     float dM[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) dM[i] = 0.f;
@@ -436,8 +433,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         for (int j = 0; j < 3; ++j) M[3 * i + j] = Rq[3 * i + j] * s[j];
 
     bool any = false;
-    bool sh_loaded = false;
-    float shc[16][3];
     // densification statistics of this Gaussian (Sec. 3.3): the running sums are loaded here, so
     // their latency overlaps the loop instead of ending every thread
     float st_grad = 0.f, st_elev = 0.f;
@@ -561,37 +556,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         gm[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
         gop += g1.y;
 
-        // colour
-        if (!sh_loaded) { load_sh<DEG>(a.sh, a.sh_coeffs, g, shc); sh_loaded = true; }
-        const float vx = m0 - V.cam[0], vy = m1 - V.cam[1], vz = m2 - V.cam[2];
-        const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
-        const float x = vx * il, y = vy * il, z = vz * il;
-        float Y[16];
-        sh_basis<DEG>(x, y, z, Y);
-        const float drgb[3] = {g1.z, g1.w, g2.x};
-        float wsum[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.5f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
-            if (acc < 0.f) continue;  // clamped channel
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                gsh[k][ch] += drgb[ch] * Y[k];
-                wsum[k] += drgb[ch] * shc[k][ch];
-            }
-        }
-        if (DEG > 0) {
-            float gx, gy, gz;
-            sh_grad_acc<DEG>(x, y, z, wsum, gx, gy, gz);
-            const float dd = gx * x + gy * y + gz * z;  // project out the radial part
-            gm[0] += (gx - dd * x) * il;
-            gm[1] += (gy - dd * y) * il;
-            gm[2] += (gz - dd * z) * il;
-        }
     }
 
     if (a.d_count && st_count != st_count0) {  // this thread owns Gaussian g
@@ -623,6 +587,51 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         gq[0] = (dw - qw * dot) / qn; gq[1] = (dx - qx * dot) / qn;
         gq[2] = (dy - qy * dot) / qn; gq[3] = (dz - qz * dot) / qn;
     }
+    // colour phase (after the geometry, so that its 96 SH registers are not live together with
+    // the covariance chain): dL/dsh and the view direction's gradient, view by view
+    float gsh[16][3];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+    if (any) {
+        float shc[16][3];
+        load_sh<DEG>(a.sh, a.sh_coeffs, g, shc);
+        for (int v = 0; v < a.n_views; ++v) {
+            const size_t item = (size_t)v * a.n + g;
+            const float4 g1 = a.acc[3 * item + 1], g2 = a.acc[3 * item + 2];
+            if (g1.z == 0.f && g1.w == 0.f && g2.x == 0.f) continue;
+            const ViewDev& V = a.views[v];
+            const float vx = m0 - V.cam[0], vy = m1 - V.cam[1], vz = m2 - V.cam[2];
+            const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+            const float x = vx * il, y = vy * il, z = vz * il;
+            float Y[16];
+            sh_basis<DEG>(x, y, z, Y);
+            const float drgb[3] = {g1.z, g1.w, g2.x};
+            float wsum[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.5f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc = fmaf(shc[k][ch], Y[k], acc);
+                if (acc < 0.f) continue;  // clamped channel
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    gsh[k][ch] += drgb[ch] * Y[k];
+                    wsum[k] += drgb[ch] * shc[k][ch];
+                }
+            }
+            if (DEG > 0) {
+                float gx, gy, gz;
+                sh_grad_acc<DEG>(x, y, z, wsum, gx, gy, gz);
+                const float dd = gx * x + gy * y + gz * z;  // project out the radial part
+                gm[0] += (gx - dd * x) * il;
+                gm[1] += (gy - dd * y) * il;
+                gm[2] += (gz - dd * z) * il;
+            }
+        }
+    }
+
     if (a.raw) {  // chain through the activations: d/dlog s = d/ds * s, d/dlogit = d/do * o (1 - o)
 #pragma unroll
         for (int i = 0; i < 3; ++i) gs[i] *= s[i];
