@@ -6,10 +6,12 @@
 // 11-tap Gaussian). Because every moment is a correlation with g, which is symmetric,
 //   dSSIM_mean / dx_p = (g * A)_p + 2 x_p (g * B)_p + y_p (g * C)_p,
 //   A = c (ds/dmx - 2 mx ds/dsxx - my ds/dsxy),  B = c ds/dsxx,  C = c ds/dsxy.
-//   k_ssim_fwd    per 32 x 16 tile and channel: the image and target with a 5-pixel halo in shared
-//                 memory, a horizontal then a vertical 11-tap pass for the five moments, then s,
-//                 the loss partial and the maps A, B, C (scratch)
+//   k_ssim_fwd    per 32 x 32 tile and channel: the image and target with a 5-pixel halo in shared
+//                 memory, a horizontal then a vertical 11-tap pass for the five moments (each thread
+//                 computes 4 outputs from the 14 inputs it loads once), then s, the loss partial
+//                 and the maps A, B, C (scratch)
 //   k_ssim_bwd    the same tiling over A, B, C: two passes, then the gradient with the L1 term
+//   k_l1          lambda = 0: the L1 term alone, one pass
 //   k_loss_reduce one CTA: the CTAs' partials in a fixed order (deterministic)
 // Rows outside the image are zero (zero padding); columns wrap around the seam or are zero.
 #include <cuda_runtime.h>
@@ -22,8 +24,11 @@ namespace {
 
 constexpr int kR = 5;
 constexpr int kWin = 2 * kR + 1;
-constexpr int kTX = 32, kTY = 16;
+constexpr int kTX = 32, kTY = 32;
 constexpr int kInW = kTX + 2 * kR, kInH = kTY + 2 * kR;
+constexpr int kLd = kInW + 1;  // odd row stride of the input tiles: rows of a warp hit distinct banks
+constexpr int kHd = kTX + 1;   // row stride of the horizontal pass's output
+constexpr int kCB = 4;         // outputs per thread in each pass (register blocking)
 constexpr int kThreads = 256;
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
@@ -44,7 +49,7 @@ __device__ __forceinline__ float row_weight(const LossArgs& a, int j) {
 }
 
 // Loads rows [y0 - kR, y0 + kTY + kR) x columns [x0 - kR, x0 + kTX + kR) of src into dst.
-__device__ __forceinline__ void load_halo(const LossArgs& a, const float* __restrict__ src, float (*dst)[kInW], int x0,
+__device__ __forceinline__ void load_halo(const LossArgs& a, const float* __restrict__ src, float (*dst)[kLd], int x0,
                                           int y0) {
     for (int i = threadIdx.x; i < kInH * kInW; i += kThreads) {
         const int r = i / kInW, q = i - r * kInW;
@@ -74,9 +79,11 @@ __device__ __forceinline__ float block_sum(float v, float* s_red) {
     return t;
 }
 
+// Forward: per channel, the 11-tap passes with register blocking (a thread computes kCB outputs
+// from the kCB + 10 inputs it loads once), then SSIM, the loss partial and the maps A, B, C.
 __global__ void __launch_bounds__(kThreads) k_ssim_fwd(LossArgs a) {
-    __shared__ float s_x[kInH][kInW], s_y[kInH][kInW];
-    __shared__ float s_h[5][kInH][kTX];
+    __shared__ float s_x[kInH][kLd], s_y[kInH][kLd];
+    __shared__ float s_h[5][kInH][kHd];
     __shared__ float s_red[kThreads / 32];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const size_t HW = (size_t)a.W * a.H;
@@ -85,50 +92,80 @@ __global__ void __launch_bounds__(kThreads) k_ssim_fwd(LossArgs a) {
         load_halo(a, a.x + c * HW, s_x, x0, y0);
         load_halo(a, a.y + c * HW, s_y, x0, y0);
         __syncthreads();
-        for (int i = threadIdx.x; i < kInH * kTX; i += kThreads) {
-            const int r = i / kTX, q = i - r * kTX;
-            float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
+        // horizontal: rows [0, kInH) x output columns [0, kTX); lanes take consecutive rows
+        for (int it = threadIdx.x; it < kInH * (kTX / kCB); it += kThreads) {
+            const int r = it % kInH, q0 = (it / kInH) * kCB;
+            float o[5][kCB];
 #pragma unroll
-            for (int k = 0; k < kWin; ++k) {
-                const float xv = s_x[r][q + k], yv = s_y[r][q + k], gk = a.g[k];
-                hx = fmaf(gk, xv, hx);
-                hy = fmaf(gk, yv, hy);
-                hxx = fmaf(gk, xv * xv, hxx);
-                hyy = fmaf(gk, yv * yv, hyy);
-                hxy = fmaf(gk, xv * yv, hxy);
+            for (int m = 0; m < 5; ++m)
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) o[m][j] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kCB + 2 * kR; ++i) {
+                const float xv = s_x[r][q0 + i], yv = s_y[r][q0 + i];
+                const float xx = xv * xv, yy = yv * yv, xy = xv * yv;
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) {
+                    const int k = i - j;
+                    if (k < 0 || k >= kWin) continue;
+                    const float gk = a.g[k];
+                    o[0][j] = fmaf(gk, xv, o[0][j]);
+                    o[1][j] = fmaf(gk, yv, o[1][j]);
+                    o[2][j] = fmaf(gk, xx, o[2][j]);
+                    o[3][j] = fmaf(gk, yy, o[3][j]);
+                    o[4][j] = fmaf(gk, xy, o[4][j]);
+                }
             }
-            s_h[0][r][q] = hx; s_h[1][r][q] = hy; s_h[2][r][q] = hxx; s_h[3][r][q] = hyy; s_h[4][r][q] = hxy;
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) s_h[m][r][q0 + j] = o[m][j];
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < kTY * kTX; i += kThreads) {
-            const int r = i / kTX, q = i - r * kTX;
-            const int gy = y0 + r, gx = x0 + q;
-            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+        // vertical: output rows [r0, r0 + kCB) of column q; lanes take consecutive columns
+        for (int it = threadIdx.x; it < kTX * (kTY / kCB); it += kThreads) {
+            const int q = it % kTX, r0 = (it / kTX) * kCB;
+            float o[5][kCB];
 #pragma unroll
-            for (int k = 0; k < kWin; ++k) {
-                const float gk = a.g[k];
-                mx = fmaf(gk, s_h[0][r + k][q], mx);
-                my = fmaf(gk, s_h[1][r + k][q], my);
-                exx = fmaf(gk, s_h[2][r + k][q], exx);
-                eyy = fmaf(gk, s_h[3][r + k][q], eyy);
-                exy = fmaf(gk, s_h[4][r + k][q], exy);
+            for (int m = 0; m < 5; ++m)
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) o[m][j] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kCB + 2 * kR; ++i) {
+                float h[5];
+#pragma unroll
+                for (int m = 0; m < 5; ++m) h[m] = s_h[m][r0 + i][q];
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) {
+                    const int k = i - j;
+                    if (k < 0 || k >= kWin) continue;
+                    const float gk = a.g[k];
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) o[m][j] = fmaf(gk, h[m], o[m][j]);
+                }
             }
-            if (gy >= a.H || gx >= a.W) continue;
-            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-            const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-            const float iB1 = 1.f / B1, iB2 = 1.f / B2;
-            const float s = A1 * A2 * iB1 * iB2;
-            const float ds_dmx = 2.f * A2 * (my * B1 - mx * A1) * iB1 * iB1 * iB2;
-            const float ds_dsxx = -s * iB2;
-            const float ds_dsxy = 2.f * A1 * iB1 * iB2;
-            const float xv = s_x[r + kR][q + kR], yv = s_y[r + kR][q + kR];
-            const float w = row_weight(a, gy) * a.inv_wsum;
-            part = fmaf(w, (1.f - a.lam) * fabsf(xv - yv) + a.lam * (1.f - s), part);
-            float* m = a.maps + (size_t)(3 * c) * HW + (size_t)gy * a.W + gx;
-            m[0] = w * (ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy);
-            m[HW] = w * ds_dsxx;
-            m[2 * HW] = w * ds_dsxy;
+            const int gx = x0 + q;
+#pragma unroll
+            for (int j = 0; j < kCB; ++j) {
+                const int gy = y0 + r0 + j;
+                if (gy >= a.H || gx >= a.W) continue;
+                const float mx = o[0][j], my = o[1][j];
+                const float sxx = o[2][j] - mx * mx, syy = o[3][j] - my * my, sxy = o[4][j] - mx * my;
+                const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+                const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+                const float iB1 = 1.f / B1, iB2 = 1.f / B2;
+                const float sv = A1 * A2 * iB1 * iB2;
+                const float ds_dmx = 2.f * A2 * (my * B1 - mx * A1) * iB1 * iB1 * iB2;
+                const float ds_dsxx = -sv * iB2;
+                const float ds_dsxy = 2.f * A1 * iB1 * iB2;
+                const float xv = s_x[r0 + j + kR][q + kR], yv = s_y[r0 + j + kR][q + kR];
+                const float w = row_weight(a, gy) * a.inv_wsum;
+                part = fmaf(w, (1.f - a.lam) * fabsf(xv - yv) + a.lam * (1.f - sv), part);
+                float* mp = a.maps + (size_t)(3 * c) * HW + (size_t)gy * a.W + gx;
+                mp[0] = w * (ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy);
+                mp[HW] = w * ds_dsxx;
+                mp[2 * HW] = w * ds_dsxy;
+            }
         }
         __syncthreads();  // the next channel overwrites the tiles
     }
@@ -136,45 +173,75 @@ __global__ void __launch_bounds__(kThreads) k_ssim_fwd(LossArgs a) {
     if (threadIdx.x == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
+// Backward: the same blocked passes over the maps A, B, C, then the gradient with the L1 term.
 __global__ void __launch_bounds__(kThreads) k_ssim_bwd(LossArgs a) {
-    __shared__ float s_m[3][kInH][kInW];
-    __shared__ float s_h[3][kInH][kTX];
+    __shared__ float s_m[3][kInH][kLd];
+    __shared__ float s_h[3][kInH][kHd];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const size_t HW = (size_t)a.W * a.H;
     for (int c = 0; c < 3; ++c) {
         for (int k = 0; k < 3; ++k) load_halo(a, a.maps + (size_t)(3 * c + k) * HW, s_m[k], x0, y0);
         __syncthreads();
-        for (int i = threadIdx.x; i < kInH * kTX; i += kThreads) {
-            const int r = i / kTX, q = i - r * kTX;
-            float h0 = 0.f, h1 = 0.f, h2 = 0.f;
+        for (int it = threadIdx.x; it < kInH * (kTX / kCB); it += kThreads) {
+            const int r = it % kInH, q0 = (it / kInH) * kCB;
+            float o[3][kCB];
 #pragma unroll
-            for (int k = 0; k < kWin; ++k) {
-                const float gk = a.g[k];
-                h0 = fmaf(gk, s_m[0][r][q + k], h0);
-                h1 = fmaf(gk, s_m[1][r][q + k], h1);
-                h2 = fmaf(gk, s_m[2][r][q + k], h2);
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) o[m][j] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kCB + 2 * kR; ++i) {
+                float v[3];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) v[m] = s_m[m][r][q0 + i];
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) {
+                    const int k = i - j;
+                    if (k < 0 || k >= kWin) continue;
+                    const float gk = a.g[k];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) o[m][j] = fmaf(gk, v[m], o[m][j]);
+                }
             }
-            s_h[0][r][q] = h0; s_h[1][r][q] = h1; s_h[2][r][q] = h2;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) s_h[m][r][q0 + j] = o[m][j];
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < kTY * kTX; i += kThreads) {
-            const int r = i / kTX, q = i - r * kTX;
-            const int gy = y0 + r, gx = x0 + q;
-            if (gy >= a.H || gx >= a.W) continue;
-            float ga = 0.f, gb = 0.f, gc = 0.f;
+        for (int it = threadIdx.x; it < kTX * (kTY / kCB); it += kThreads) {
+            const int q = it % kTX, r0 = (it / kTX) * kCB;
+            float o[3][kCB];
 #pragma unroll
-            for (int k = 0; k < kWin; ++k) {
-                const float gk = a.g[k];
-                ga = fmaf(gk, s_h[0][r + k][q], ga);
-                gb = fmaf(gk, s_h[1][r + k][q], gb);
-                gc = fmaf(gk, s_h[2][r + k][q], gc);
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) o[m][j] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kCB + 2 * kR; ++i) {
+                float h[3];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) h[m] = s_h[m][r0 + i][q];
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) {
+                    const int k = i - j;
+                    if (k < 0 || k >= kWin) continue;
+                    const float gk = a.g[k];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) o[m][j] = fmaf(gk, h[m], o[m][j]);
+                }
             }
-            const size_t pix = c * HW + (size_t)gy * a.W + gx;
-            const float xv = a.x[pix], yv = a.y[pix];
-            const float d = xv - yv;
-            const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            const float w = row_weight(a, gy) * a.inv_wsum;
-            a.grad[pix] = (1.f - a.lam) * w * sgn - a.lam * (ga + 2.f * xv * gb + yv * gc);
+            const int gx = x0 + q;
+#pragma unroll
+            for (int j = 0; j < kCB; ++j) {
+                const int gy = y0 + r0 + j;
+                if (gy >= a.H || gx >= a.W) continue;
+                const size_t pix = c * HW + (size_t)gy * a.W + gx;
+                const float xv = a.x[pix], yv = a.y[pix];
+                const float d = xv - yv;
+                const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                const float w = row_weight(a, gy) * a.inv_wsum;
+                a.grad[pix] = (1.f - a.lam) * w * sgn - a.lam * (o[0][j] + 2.f * xv * o[1][j] + yv * o[2][j]);
+            }
         }
         __syncthreads();
     }
