@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--width", type=int, default=2048)
     ap.add_argument("--tile", type=str, default="16x16")
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the blend kernels (0 = auto)")
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the forward blend (0 = auto)")
+    ap.add_argument("--ppt-bwd", type=int, default=0, help="pixels per thread in the backward blend (0 = auto)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view batched measurement")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-next", action="store_true", help="skip the measurements of the steps after the hot path")
@@ -442,8 +443,10 @@ def run_cubemap(torch, dev, params, target_erp, rs, steps=20, warmup=3):
     3DGS(P)-style cubemap alternative to the ERP view."""
     from paper_2410_20686_gb300 import scenes as S
     from paper_2410_20686_gb300.graph import GraphedFrame
-    faces = S.cubemap_views(592)
-    targets = [torch.rand((3, 592, 592), device=dev, generator=torch.Generator(device=dev).manual_seed(k))
+    # faces of about the ERP view's pixel count, a multiple of the tile width
+    face = max(rs.tile_w, int(round((2048 * 1024 / 6) ** 0.5 / rs.tile_w)) * rs.tile_w)
+    faces = S.cubemap_views(face)
+    targets = [torch.rand((3, face, face), device=dev, generator=torch.Generator(device=dev).manual_seed(k))
                for k in range(6)]
     gf = GraphedFrame(params, faces, targets, rs)
     for _ in range(warmup):
@@ -457,8 +460,9 @@ def run_cubemap(torch, dev, params, target_erp, rs, steps=20, warmup=3):
     torch.cuda.synchronize(dev)
     assert gf.status() == 0
     ms = e0.elapsed_time(e1) / steps
-    return {"workload": "1M Gaussians, six 592x592 pinhole cube faces (2.10 Mpx), fwd+bwd with L1 loss, one graph",
-            "ms_per_frame": ms, "iter_per_s": 1e3 / ms, "pixels": 6 * 592 * 592}
+    return {"workload": f"1M Gaussians, six {face}x{face} pinhole cube faces ({6 * face * face / 1e6:.2f} Mpx), "
+                        "fwd+bwd with L1 loss, one graph",
+            "ms_per_frame": ms, "iter_per_s": 1e3 / ms, "pixels": 6 * face * face}
 
 
 # ------------------------------------------------------------------ multi-process plumbing
@@ -509,7 +513,8 @@ def run_ours(args):
             dist.barrier()
 
     tw, th = (int(x) for x in args.tile.split("x"))
-    rs = RenderSettings(sh_degree=3, tile_w=tw, tile_h=th, batch=args.batch, pixels_per_thread=args.ppt)
+    rs = RenderSettings(sh_degree=3, tile_w=tw, tile_h=th, batch=args.batch, pixels_per_thread=args.ppt,
+                        pixels_per_thread_bwd=args.ppt_bwd)
     scene = S.config2(n=args.n, width=args.width)
     target_np = S.target_images(scene, 2)[0]
     view = scene.views[0]
@@ -637,6 +642,7 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2,
                       "sh_degree": 3, "tile": args.tile, "batch": args.batch, "pixels_per_thread": args.ppt,
+                      "pixels_per_thread_bwd": args.ppt_bwd,
                       "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
                       "parallelism": f"replicas x{world}"},
            "roofline": roofline, "kernels_ms": kern, "kernels": kernels, "gpu_launches": launches_per_step * K,

@@ -85,13 +85,17 @@ typedef struct {
                            pair buffer last given to odgs_bin_sort, which the caller may
                            reuse for other frames between the forward and backward passes */
     int grad_accumulate;/* 1: gradients are added (+=) to the output arrays; 0: written  */
-    int pixels_per_thread; /* blend kernels: pixels of one row per thread, 1, 2, 4 or 8;
-                              0 -> the largest that divides tile_w while tile_w * tile_h /
-                              pixels_per_thread is a multiple of 32 and at most 256         */
+    int pixels_per_thread; /* forward blend: pixels of one row per thread, 1, 2, 4 or 8, such
+                              that it divides tile_w and tile_w * tile_h / pixels_per_thread is
+                              a multiple of 32 and at most 256; 0 -> 2 if that fits, else the
+                              largest of 4, 2, 1 that does                                     */
     int raw_params;     /* 1: odgs_gaussians.scales hold log-scales and .opacity logits, the
                            variables 3DGS optimises; the library applies exp and the sigmoid
                            and odgs_preprocess_bwd returns the gradients w.r.t. these raw
                            variables. 0: activated values (scales > 0, opacity in (0, 1)) */
+    int pixels_per_thread_bwd; /* backward blend, the same choices; 0 -> 4 if that fits, else the
+                                  largest of 4, 2, 1 that does. Per-pixel results do not depend
+                                  on either value                                           */
 } odgs_settings;
 
 /* Gaussian parameters, device pointers, float32, contiguous:

@@ -43,7 +43,7 @@ class Settings(C.Structure):
     _fields_ = [("sh_degree", C.c_int), ("sh_coeffs", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int),
                 ("batch", C.c_int), ("cov_dilation", C.c_float), ("r_near", C.c_float), ("r_far", C.c_float),
                 ("bg", C.c_float * 3), ("recompute_lists", C.c_int), ("grad_accumulate", C.c_int),
-                ("pixels_per_thread", C.c_int), ("raw_params", C.c_int)]
+                ("pixels_per_thread", C.c_int), ("raw_params", C.c_int), ("pixels_per_thread_bwd", C.c_int)]
 
 
 class Gaussians(C.Structure):

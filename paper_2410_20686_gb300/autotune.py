@@ -1,5 +1,5 @@
 """Autotuner for the blend launch configuration: tile shape, shared-memory batch size and pixels
-per thread.
+per thread of the forward and of the backward blend.
 
 Every candidate renders the same frame (forward + backward) a few times; the fastest one wins
 and is cached in a JSON file keyed by the workload's signature (view sizes, Gaussian count
@@ -35,13 +35,15 @@ def valid(tile_w: int, tile_h: int, ppt: int, widths) -> bool:
 
 
 def candidates(widths, tiles=TILES, batches=BATCHES, ppts=PPTS):
+    """(tile_w, tile_h, batch, forward pixels per thread, backward pixels per thread)."""
     out = []
     for (tw, th) in tiles:
-        for ppt in ppts:
-            if not valid(tw, th, ppt, widths):
-                continue
-            for b in batches:
-                out.append((tw, th, b, ppt))
+        for pf in ppts:
+            for pb in ppts:
+                if not (valid(tw, th, pf, widths) and valid(tw, th, pb, widths)):
+                    continue
+                for b in batches:
+                    out.append((tw, th, b, pf, pb))
     return out
 
 
@@ -68,7 +70,8 @@ def _time_frame(rast, params, views, rs, grads, iters):
 
 def autotune(params, views, base: RenderSettings = None, cache_path: str = DEFAULT_CACHE, iters: int = 3,
              cands=None, use_cache: bool = True, verbose: bool = False) -> RenderSettings:
-    """Fastest (tile_w, tile_h, batch, pixels_per_thread) for this frame, from the cache when known."""
+    """Fastest (tile_w, tile_h, batch, pixels per thread forward / backward) for this frame, from the
+    cache when known."""
     base = base or RenderSettings()
     key = signature(params[0].shape[0], views, base.sh_degree)
     cache = {}
@@ -80,25 +83,27 @@ def autotune(params, views, base: RenderSettings = None, cache_path: str = DEFAU
             cache = {}
     if use_cache and key in cache:
         c = cache[key]
-        return replace(base, tile_w=c["tile_w"], tile_h=c["tile_h"], batch=c["batch"], pixels_per_thread=c["ppt"])
+        return replace(base, tile_w=c["tile_w"], tile_h=c["tile_h"], batch=c["batch"], pixels_per_thread=c["ppt"],
+                       pixels_per_thread_bwd=c.get("ppt_bwd", c["ppt"]))
     cands = cands or candidates([v.width for v in views])
     rast = Rasterizer(params[0].device, capacity_mode="query")
     grads = {k: torch.empty_like(t) for k, t in zip(("means", "scales", "quats", "opacity", "sh"), params)}
     best, best_ms, results = None, float("inf"), []
-    for (tw, th, b, ppt) in cands:
-        rs = replace(base, tile_w=tw, tile_h=th, batch=b, pixels_per_thread=ppt)
+    for (tw, th, b, pf, pb) in cands:
+        rs = replace(base, tile_w=tw, tile_h=th, batch=b, pixels_per_thread=pf, pixels_per_thread_bwd=pb)
         ms = _time_frame(rast, params, views, rs, grads, iters)
-        results.append({"tile_w": tw, "tile_h": th, "batch": b, "ppt": ppt, "ms": ms})
+        results.append({"tile_w": tw, "tile_h": th, "batch": b, "ppt": pf, "ppt_bwd": pb, "ms": ms})
         if verbose:
-            print(f"autotune {tw}x{th} batch {b} ppt {ppt}: {ms:.3f} ms", flush=True)
+            print(f"autotune {tw}x{th} batch {b} ppt {pf}/{pb}: {ms:.3f} ms", flush=True)
         if ms < best_ms:
-            best, best_ms = (tw, th, b, ppt), ms
-    tw, th, b, ppt = best
+            best, best_ms = (tw, th, b, pf, pb), ms
+    tw, th, b, pf, pb = best
     if cache_path:
-        cache[key] = {"tile_w": tw, "tile_h": th, "batch": b, "ppt": ppt, "ms": best_ms, "tried": len(results)}
+        cache[key] = {"tile_w": tw, "tile_h": th, "batch": b, "ppt": pf, "ppt_bwd": pb, "ms": best_ms,
+                      "tried": len(results)}
         os.makedirs(os.path.dirname(cache_path) or ".", exist_ok=True)
         tmp = cache_path + f".tmp{os.getpid()}"
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
         os.replace(tmp, cache_path)
-    return replace(base, tile_w=tw, tile_h=th, batch=b, pixels_per_thread=ppt)
+    return replace(base, tile_w=tw, tile_h=th, batch=b, pixels_per_thread=pf, pixels_per_thread_bwd=pb)

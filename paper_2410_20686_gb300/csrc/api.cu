@@ -94,8 +94,9 @@ odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
     if (!(t.tile_w == 8 || t.tile_w == 16 || t.tile_w == 32)) return ODGS_ERR_INVALID_ARG;
     const int area = t.tile_w * t.tile_h;
     if (t.tile_h < 1 || area < 32 || area > 1024 || area % 32 != 0) return ODGS_ERR_INVALID_ARG;
-    t.pixels_per_thread = pixels_per_thread(t.tile_w, t.tile_h, t.pixels_per_thread);
-    if (t.pixels_per_thread == 0) return ODGS_ERR_INVALID_ARG;
+    t.pixels_per_thread = pixels_per_thread(t.tile_w, t.tile_h, t.pixels_per_thread, 2);
+    t.pixels_per_thread_bwd = pixels_per_thread(t.tile_w, t.tile_h, t.pixels_per_thread_bwd, 4);
+    if (t.pixels_per_thread == 0 || t.pixels_per_thread_bwd == 0) return ODGS_ERR_INVALID_ARG;
     if (t.batch == 0) t.batch = 64;
     if (t.batch < 1 || t.batch > 256) return ODGS_ERR_INVALID_ARG;
     if (!finite(t.cov_dilation) || t.cov_dilation < 0.f) return ODGS_ERR_INVALID_ARG;
@@ -280,7 +281,7 @@ odgs_status odgs_preprocess(odgs_ctx* c, const odgs_gaussians* g, const odgs_vie
     c->stage = 0;
     c->launches = 0;
     c->bwd_batch = std::min(st.batch, 64);
-    const int bwd_threads = st.tile_w * st.tile_h / st.pixels_per_thread;
+    const int bwd_threads = st.tile_w * st.tile_h / st.pixels_per_thread_bwd;
     while (c->bwd_batch > 8 && render_bwd_smem(c->bwd_batch, bwd_threads) > 48 * 1024) c->bwd_batch /= 2;
     r = run_preprocess(c, static_cast<cudaStream_t>(stream));
     if (r != ODGS_OK) return r;
@@ -444,7 +445,7 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
     a.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
     a.n_views = c->V; a.total_tiles = c->geo.total_tiles;
     a.tile_w = c->s.tile_w; a.tile_h = c->s.tile_h; a.batch = c->bwd_batch;
-    a.ppt = c->s.pixels_per_thread;
+    a.ppt = c->s.pixels_per_thread_bwd;
     a.n_items = (uint32_t)c->geo.n_items;
     a.ranges = reinterpret_cast<const uint2*>(w + c->L.ranges);
     a.pair_vals = c->sorted_vals;

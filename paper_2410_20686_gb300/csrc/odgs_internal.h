@@ -153,7 +153,9 @@ size_t render_fwd_smem(int batch);
 size_t render_bwd_smem(int batch, int threads);
 // Pixels per thread of the blend kernels for a tile shape: `want` (1, 2, 4) if it fits, the
 // largest that fits when want == 0, and 0 when the shape (or the wish) is not supported.
-int pixels_per_thread(int tile_w, int tile_h, int want = 0);
+// Pixels per thread of a blend kernel: want if valid (0 if not), or for want = 0 `prefer` if it
+// fits the tile, else the largest of 4, 2, 1 that does. The forward prefers 2, the backward 4.
+int pixels_per_thread(int tile_w, int tile_h, int want, int prefer);
 int render_fwd_occupancy(int tile_w, int tile_h, int batch, int ppt);
 int render_bwd_occupancy(int tile_w, int tile_h, int batch, int ppt);
 cudaError_t launch_render_fwd(const FwdArgs& a, int grid, cudaStream_t st);

@@ -168,10 +168,11 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
 
 size_t render_fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4) + sizeof(float)); }
 
-int pixels_per_thread(int tile_w, int tile_h, int want) {
+int pixels_per_thread(int tile_w, int tile_h, int want, int prefer) {
     const int area = tile_w * tile_h;
     auto fits = [&](int p) { return tile_w % p == 0 && (area / p) % 32 == 0 && area / p <= 256; };
     if (want != 0) return (want == 1 || want == 2 || want == 4 || want == 8) && fits(want) ? want : 0;
+    if (fits(prefer)) return prefer;
     for (int p = 4; p >= 1; p >>= 1)
         if (fits(p)) return p;
     return 0;

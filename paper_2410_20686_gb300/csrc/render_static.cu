@@ -74,7 +74,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     if (!(st.tile_w == 8 || st.tile_w == 16 || st.tile_w == 32) || st.tile_h < 1 ||
         st.tile_w * st.tile_h < 32 || st.tile_w * st.tile_h > 1024 || (st.tile_w * st.tile_h) % 32 != 0)
         return ODGS_ERR_INVALID_ARG;
-    st.pixels_per_thread = pixels_per_thread(st.tile_w, st.tile_h, st.pixels_per_thread);
+    st.pixels_per_thread = pixels_per_thread(st.tile_w, st.tile_h, st.pixels_per_thread, 2);
     if (st.pixels_per_thread == 0) return ODGS_ERR_INVALID_ARG;
     if (st.batch < 1 || st.batch > 256) return ODGS_ERR_INVALID_ARG;
     if (!(st.cov_dilation >= 0.f) || !(st.r_near >= 0.f) || !(st.r_far > st.r_near)) return ODGS_ERR_INVALID_ARG;

@@ -26,8 +26,9 @@ class RenderSettings:
     bg: tuple = (0.0, 0.0, 0.0)
     recompute_lists: bool = False
     grad_accumulate: bool = False
-    pixels_per_thread: int = 0
+    pixels_per_thread: int = 0      # forward blend (0: automatic, 2 where it fits)
     raw_params: bool = False  # scales are log-scales and opacity logits (activated by the kernels)
+    pixels_per_thread_bwd: int = 0  # backward blend (0: automatic, 4 where it fits)
 
     def c_struct(self, sh_coeffs: int) -> L.Settings:
         s = L.Settings()
@@ -39,6 +40,7 @@ class RenderSettings:
         s.grad_accumulate = int(bool(self.grad_accumulate))
         s.pixels_per_thread = int(self.pixels_per_thread)
         s.raw_params = int(bool(self.raw_params))
+        s.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
         return s
 
 

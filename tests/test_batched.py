@@ -24,10 +24,10 @@ def test_autotune_candidates_pass_the_library_validation():
     cands = A.candidates(widths, tiles=((16, 16), (16, 8), (32, 8), (8, 8), (32, 16), (16, 32), (8, 4), (32, 32)),
                          ppts=(1, 2, 4))
     assert len(cands) > 20
-    for tw, th, b, ppt in cands:
-        st = RenderSettings(tile_w=tw, tile_h=th, batch=b, pixels_per_thread=ppt).c_struct(16)
+    for tw, th, b, pf, pb in cands:
+        st = RenderSettings(tile_w=tw, tile_h=th, batch=b, pixels_per_thread=pf, pixels_per_thread_bwd=pb).c_struct(16)
         out = C.c_size_t()
-        assert lib.odgs_workspace_size(1000, views, 3, C.byref(st), C.byref(out)) == 0, (tw, th, b, ppt)
+        assert lib.odgs_workspace_size(1000, views, 3, C.byref(st), C.byref(out)) == 0, (tw, th, b, pf, pb)
     # and a shape the tuner rejects is rejected by the library too
     st = RenderSettings(tile_w=32, tile_h=32, pixels_per_thread=1).c_struct(16)
     assert not A.valid(32, 32, 1, widths)
@@ -92,10 +92,10 @@ def test_autotune_picks_and_caches(tmp_path):
     sc = S.random_scene(2000, 256, 128, seed=303, sh_degree=1)
     params = [torch.tensor(a, device="cuda") for a in (sc.means, sc.scales, sc.quats, sc.opacity, sc.sh)]
     cache = str(tmp_path / "tune.json")
-    cands = [(16, 16, 64, 4), (16, 8, 32, 2), (32, 8, 64, 4)]
+    cands = [(16, 16, 64, 4, 4), (16, 8, 32, 2, 4), (32, 8, 64, 4, 2), (16, 16, 64, 2, 4)]
     rs = A.autotune(params, sc.views, RenderSettings(sh_degree=1), cache_path=cache, iters=2, cands=cands)
-    assert (rs.tile_w, rs.tile_h, rs.batch, rs.pixels_per_thread) in cands
-    again = A.autotune(params, sc.views, RenderSettings(sh_degree=1), cache_path=cache, cands=[(8, 8, 32, 2)])
+    assert (rs.tile_w, rs.tile_h, rs.batch, rs.pixels_per_thread, rs.pixels_per_thread_bwd) in cands
+    again = A.autotune(params, sc.views, RenderSettings(sh_degree=1), cache_path=cache, cands=[(8, 8, 32, 2, 2)])
     assert (again.tile_w, again.tile_h) == (rs.tile_w, rs.tile_h)  # served from the cache
 
 
