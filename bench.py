@@ -189,23 +189,38 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
 
 
 # DRAM bytes (read + write) of one k_render_bwd launch on this workload from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid while the kernel's sources hash to the
-# recorded value; after any change the bench reports null until it is captured again.
-PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh", "odgs_internal.h"),
-                    "sha256": "ae63dd00f1b9486f1d7b4f67ba1e4ed8f1144a85f903545be87c7f575adf448f",
-                    "bytes": 171399424}
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid while the kernel's sources (its file, the
+# shared device header and its argument struct) hash to the recorded value; after any change the
+# bench reports null until it is captured again.
+PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh"),
+                    "structs": ("odgs_internal.h", "BwdArgs"),
+                    "sha256": "685cd889e54571c72ac0dbbede7b89b9630b2e43a4cebb01ec4ae44009f9766a",
+                    "bytes": 170767104}
+
+
+def kernel_sources_digest(spec=PROFILED_TRAFFIC):
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_20686_gb300", "csrc")
+    try:
+        for f in spec["sources"]:
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+        header, name = spec["structs"]
+        with open(os.path.join(csrc, header)) as fh:
+            m = re.search(r"struct %s \{.*?\n\};" % name, fh.read(), re.S)
+        if m is None:
+            return None
+        h.update(m.group(0).encode())
+    except OSError:
+        return None
+    return h.hexdigest()
 
 
 def profiled_traffic():
-    import hashlib
-    h = hashlib.sha256()
-    try:
-        for f in PROFILED_TRAFFIC["sources"]:
-            with open(os.path.join(ROOT, "paper_2410_20686_gb300", "csrc", f), "rb") as fh:
-                h.update(fh.read())
-    except OSError:
-        return None
-    if PROFILED_TRAFFIC["sha256"] and h.hexdigest() == PROFILED_TRAFFIC["sha256"]:
+    d = kernel_sources_digest()
+    if d is not None and PROFILED_TRAFFIC["sha256"] and d == PROFILED_TRAFFIC["sha256"]:
         return PROFILED_TRAFFIC["bytes"]
     return None
 
@@ -525,10 +540,11 @@ def run_ours(args):
 
     evs = None
 
-    def step(record=None):
+    def step(record=None, inputs=None):
+        p, tgt = (params, target) if inputs is None else (inputs[:5], inputs[5])
         if record is not None:
             record[0].record()
-        rast.preprocess(*params, [view], rs)
+        rast.preprocess(*p, [view], rs)
         if record is not None:
             record[1].record()
         rast.bin_sort()
@@ -538,7 +554,7 @@ def run_ours(args):
         if record is not None:
             record[3].record()
         # mean absolute error and its gradient sign(C - target) / (3 W H), one fused kernel
-        loss, gl = l1_dssim([imgs[0]], [target], lam=0.0, area_weight=False)
+        loss, gl = l1_dssim([imgs[0]], [tgt], lam=0.0, area_weight=False)
         g = gl[0]
         if record is not None:
             record[4].record()
@@ -587,30 +603,60 @@ def run_ours(args):
     names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
     kern = {nm: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)])) for j, nm in enumerate(names)}
 
-    # end-to-end through host buffers: parameters and target copied in from pinned memory each
-    # step, the loss read back
+    # end-to-end through host buffers: every step copies its parameters and target in from pinned
+    # host memory and reads its loss back. The copies run on a second stream into one of two device
+    # input sets, so step i+1's upload overlaps step i's kernels (a data loader's prefetch); the
+    # first upload and the last loss read are inside the timed region.
     e2e = None
     if not args.no_e2e:
         host = [t_.cpu().pin_memory() for t_ in params] + [target.cpu().pin_memory()]
-        dev_bufs = params + [target]
+        sets = [params + [target], [torch.empty_like(h, device=dev) for h in host]]
         h2d = sum(h.numel() * h.element_size() for h in host)
+        copy_stream = torch.cuda.Stream(dev)
+        main = torch.cuda.current_stream(dev)
+        loaded = [torch.cuda.Event() for _ in sets]
+        freed = [torch.cuda.Event() for _ in sets]
+        loss_host = [torch.empty((), dtype=torch.float32).pin_memory() for _ in sets]
+        read = [torch.cuda.Event() for _ in sets]
 
-        def e2e_step():
-            for h, d in zip(host, dev_bufs):
-                d.copy_(h, non_blocking=True)
-            loss = step()
-            return loss.item()
-        for _ in range(max(1, args.warmup // 2)):
-            e2e_step()
+        def upload(j):
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(freed[j])  # the step that last read set j has finished
+                for h, d in zip(host, sets[j]):
+                    d.copy_(h, non_blocking=True)
+                loaded[j].record(copy_stream)
+
+        def run_e2e(steps):
+            losses = []
+            for j in range(2):
+                freed[j].record(main)
+            upload(0)
+            for i in range(steps):
+                j = i % 2
+                if i + 1 < steps:
+                    upload(1 - j)
+                main.wait_event(loaded[j])
+                loss = step(inputs=sets[j])
+                freed[j].record(main)
+                loss_host[j].copy_(loss, non_blocking=True)
+                read[j].record(main)
+                if i > 0:  # the previous step's loss, read while this step runs
+                    read[1 - j].synchronize()
+                    losses.append(float(loss_host[1 - j]))
+            read[(steps - 1) % 2].synchronize()
+            losses.append(float(loss_host[(steps - 1) % 2]))
+            return losses
+        run_e2e(max(3, args.warmup))
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(K):
-            e2e_step()
+        losses = run_e2e(K)
         torch.cuda.synchronize()
         barrier()
         te = max_over_ranks(time.perf_counter() - t0, world, dev)
-        e2e = {"value": job_rate(world, K, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+        assert len(losses) == K and all(np.isfinite(losses)), losses
+        e2e = {"value": job_rate(world, K, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
+               "overlap": "uploads on a second stream, double-buffered; losses read one step behind"}
 
     if rank != 0:
         if world > 1:
