@@ -151,8 +151,6 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const Header* hdr, uint2* r
 
 size_t render_fwd_smem(int batch);
 size_t render_bwd_smem(int batch, int threads);
-// Pixels per thread of the blend kernels for a tile shape: `want` (1, 2, 4) if it fits, the
-// largest that fits when want == 0, and 0 when the shape (or the wish) is not supported.
 // Pixels per thread of a blend kernel: want if valid (0 if not), or for want = 0 `prefer` if it
 // fits the tile, else the largest of 4, 2, 1 that does. The forward prefers 2, the backward 4.
 int pixels_per_thread(int tile_w, int tile_h, int want, int prefer);
