@@ -243,6 +243,18 @@ __device__ __forceinline__ void footprint_rows(const Footprint& f, int H, int& j
     jhi = min(H - 1, f.r0 + (int)floorf(__fadd_rn(f.dv, ev)));
 }
 
+// The same rows from the records directly, without the rest of the footprint: the backward blend
+// skips an entry for a warp whose pixel rows all lie outside them (x = jlo, y = jhi). The
+// operations are footprint_rows(make_footprint(ra, rb), H)'s, so the rows are the same.
+__device__ __forceinline__ int2 footprint_row_range(float4 ra, float4 rb, int H) {
+    int c0, r0;
+    unpack_anchor(ra.z, c0, r0);
+    const float det = __fsub_rn(__fmul_rn(rb.x, rb.z), __fmul_rn(rb.y, rb.y));
+    const float C = __fdiv_rn(rb.x, det);
+    const float ev = fminf(__fsqrt_rn(__fmul_rn(rb.w, C)), 2.f * (float)H);
+    return make_int2(max(0, r0 + (int)ceilf(__fsub_rn(ra.y, ev))), min(H - 1, r0 + (int)floorf(__fadd_rn(ra.y, ev))));
+}
+
 // Horizontal offset of the slice boundary at vertical offset y (side = +1 right, -1 left).
 __device__ __forceinline__ float slice_edge(const Footprint& f, float y, float side) {
     const float q = fmaxf(__fsub_rn(f.Qb, __fdiv_rn(__fmul_rn(y, y), f.C)), 0.f);

@@ -13,8 +13,10 @@
 // A thread first sums the nine values over its PPT pixels; the warp then sums them over its
 // lanes with a transpose reduction (12 shuffles for 9 values), the CTA over its warps in shared
 // memory, and the result is added to the per-(view, Gaussian) accumulator with three 16-byte
-// vector atomics. A warp whose pixels all stopped before an entry skips it; a warp with a single
-// contributing lane skips the reduction.
+// vector atomics. A warp whose pixels all stopped before an entry skips it, and so does a warp
+// none of whose pixel rows lies within the entry's footprint rows (the rows the binning lists the
+// Gaussian in; outside them no pixel reaches alpha = 1/255); a warp with a single contributing
+// lane skips the reduction.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
@@ -69,7 +71,8 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
     float4* s_con = smem + B;
     float4* s_col = smem + 2 * B;
     float4* s_raw = smem + 3 * B;  // conic a, b, c, 1 / opacity
-    float* s_fc2 = reinterpret_cast<float*>(smem + 4 * B);
+    int2* s_rows = reinterpret_cast<int2*>(smem + 4 * B);  // pixel rows the footprint reaches
+    float* s_fc2 = reinterpret_cast<float*>(s_rows + B);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_fc2 + B);
     float* s_red = reinterpret_cast<float*>(s_idx + B);  // [B][nwarps][9]
     __shared__ int s_item;
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
     const int tw = a.tile_w;
     const int tpr = tw / PPT;
     const int lx0 = (tid % tpr) * PPT, ly = tid / tpr;
+    const int wy0 = (warp << 5) / tpr, wy1 = ((warp << 5) + 31) / tpr;  // the warp's tile rows
     uint32_t evals = 0u;
 
     for (;;) {
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
         const bool inside = y < V.H;
         const float fi0 = (float)xp, fj = (float)y;
         const uint2 rg = a.ranges[item];
+        const int wr0 = ty * a.tile_h + wy0, wr1 = ty * a.tile_h + wy1;
 
         float T[PPT], Bg[PPT], g0[PPT], g1[PPT], g2[PPT];
         int nl[PPT];
@@ -139,13 +144,17 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                 s_fc2[j] = s.fc2;
                 s_raw[j] = make_float4(rb.x, rb.y, rb.z, ra.w > 0.f ? 1.f / ra.w : 0.f);
                 s_idx[j] = idx < a.n_items ? idx : 0u;
+                s_rows[j] = footprint_row_range(ra, rb, V.H);
                 split |= (s.col.w <= 1e30f);
             }
             const int any_split = __syncthreads_or(split);
             for (int j = cnt - 1; j >= 0; --j) {
                 const int e = lo + j;
                 float* red = s_red + ((size_t)j * nwarps + warp) * 9;
-                if (e >= wmax) {  // no pixel of this warp reached entry e in the forward pass
+                const int2 rows = s_rows[j];
+                // no pixel of this warp reached entry e in the forward pass, or none of its rows is
+                // within the footprint's rows
+                if (e >= wmax || rows.y < wr0 || rows.x > wr1) {
                     if (lane < 9) red[lane] = 0.f;
                     continue;
                 }
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
 }
 
 size_t render_bwd_smem(int batch, int threads) {
-    return (size_t)batch * (4 * sizeof(float4) + sizeof(float) + sizeof(uint32_t)) +
+    return (size_t)batch * (4 * sizeof(float4) + sizeof(int2) + sizeof(float) + sizeof(uint32_t)) +
            (size_t)batch * (threads / 32) * 9 * sizeof(float);
 }
 
