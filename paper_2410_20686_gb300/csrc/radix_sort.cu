@@ -40,7 +40,15 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
         const uint32_t idx = base + lane;
         const bool valid = idx < n;
         const uint32_t k = valid ? keys[idx] : 0u;
-        for (int p = 0; p < n_passes; ++p) {
+        // the low digits of the keys (depths, tile ids) are spread over many bins: one shared
+        // atomic per key; the top digit takes few values (the exponent byte of a positive float
+        // depth), so equal digits of the warp are counted with one atomic
+        for (int p = 0; p + 1 < n_passes; ++p) {
+            const uint32_t d = (k >> (begin_bit + 8 * p)) & 0xFFu;
+            if (valid) atomicAdd(&h[p][d], 1u);
+        }
+        {
+            const int p = n_passes - 1;
             const uint32_t d = (k >> (begin_bit + 8 * p)) & 0xFFu;
             const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
             if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
