@@ -7,7 +7,7 @@
 //   dSSIM_mean / dx_p = (g * A)_p + 2 x_p (g * B)_p + y_p (g * C)_p,
 //   A = c (ds/dmx - 2 mx ds/dsxx - my ds/dsxy),  B = c ds/dsxx,  C = c ds/dsxy.
 //   k_ssim_fwd    per 32 x 32 tile and channel: the image and target with a 5-pixel halo in shared
-//                 memory, a horizontal then a vertical 11-tap pass for the five moments (each thread
+//                 memory (cp.async, double-buffered: the next channel loads while this one computes), a horizontal then a vertical 11-tap pass for the five moments (each thread
 //                 computes 4 outputs from the 14 inputs it loads once), then s, the loss partial
 //                 and the maps A, B, C (scratch)
 //   k_ssim_bwd    the same tiling over A, B, C: two passes, then the gradient with the L1 term
@@ -48,26 +48,32 @@ __device__ __forceinline__ float row_weight(const LossArgs& a, int j) {
     return a.area ? sinpif(((float)j + 0.5f) / (float)a.H) : 1.f;
 }
 
-// Loads rows [y0 - kR, y0 + kTY + kR) x columns [x0 - kR, x0 + kTX + kR) of src into dst.
-__device__ __forceinline__ void load_halo(const LossArgs& a, const float* __restrict__ src, float (*dst)[kLd], int x0,
-                                          int y0) {
+// Copies rows [y0 - kR, y0 + kTY + kR) x columns [x0 - kR, x0 + kTX + kR) of src into dst with
+// asynchronous 4-byte copies (cp.async; zero-filled outside the image): the caller commits the
+// group and waits for it later, so the copy overlaps the previous channel's passes.
+__device__ __forceinline__ void load_halo_async(const LossArgs& a, const float* __restrict__ src, float (*dst)[kLd],
+                                                int x0, int y0) {
     for (int i = threadIdx.x; i < kInH * kInW; i += kThreads) {
         const int r = i / kInW, q = i - r * kInW;
         const int gy = y0 + r - kR;
         int gx = x0 + q - kR;
-        float v = 0.f;
-        if (gy >= 0 && gy < a.H) {
-            if (a.wrap) {
-                gx %= a.W;
-                if (gx < 0) gx += a.W;
-                v = src[(size_t)gy * a.W + gx];
-            } else if (gx >= 0 && gx < a.W) {
-                v = src[(size_t)gy * a.W + gx];
-            }
+        bool ok = gy >= 0 && gy < a.H;
+        if (a.wrap) {  // gx lies in [-5, W + 36]: one wrap unless the image is narrower than that
+            if (gx < 0) gx += a.W;
+            else if (gx >= a.W) gx -= a.W;
+            if (gx < 0 || gx >= a.W) gx = ((gx % a.W) + a.W) % a.W;
+        } else {
+            ok = ok && gx >= 0 && gx < a.W;
         }
-        dst[r][q] = v;
+        const float* g = ok ? src + (size_t)gy * a.W + gx : src;
+        const unsigned d = (unsigned)__cvta_generic_to_shared(&dst[r][q]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(g), "r"(ok ? 4 : 0) : "memory");
     }
 }
+
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ float block_sum(float v, float* s_red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -82,16 +88,31 @@ __device__ __forceinline__ float block_sum(float v, float* s_red) {
 // Forward: per channel, the 11-tap passes with register blocking (a thread computes kCB outputs
 // from the kCB + 10 inputs it loads once), then SSIM, the loss partial and the maps A, B, C.
 __global__ void __launch_bounds__(kThreads) k_ssim_fwd(LossArgs a) {
-    __shared__ float s_x[kInH][kLd], s_y[kInH][kLd];
-    __shared__ float s_h[5][kInH][kHd];
+    // dynamic shared memory (above the 48 KB static limit): input tiles double-buffered over the
+    // channels, then the horizontal pass's five moments
+    extern __shared__ float s_dyn[];
+    float (*s_xb)[kInH][kLd] = reinterpret_cast<float (*)[kInH][kLd]>(s_dyn);
+    float (*s_yb)[kInH][kLd] = s_xb + 2;
+    float (*s_h)[kInH][kHd] = reinterpret_cast<float (*)[kInH][kHd]>(s_yb + 2);
     __shared__ float s_red[kThreads / 32];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const size_t HW = (size_t)a.W * a.H;
     float part = 0.f;
+    load_halo_async(a, a.x, s_xb[0], x0, y0);
+    load_halo_async(a, a.y, s_yb[0], x0, y0);
+    async_commit();
     for (int c = 0; c < 3; ++c) {
-        load_halo(a, a.x + c * HW, s_x, x0, y0);
-        load_halo(a, a.y + c * HW, s_y, x0, y0);
+        if (c < 2) {  // the next channel's tiles load while this one computes
+            load_halo_async(a, a.x + (c + 1) * HW, s_xb[(c + 1) & 1], x0, y0);
+            load_halo_async(a, a.y + (c + 1) * HW, s_yb[(c + 1) & 1], x0, y0);
+            async_commit();
+            async_wait<1>();
+        } else {
+            async_wait<0>();
+        }
         __syncthreads();
+        float (*s_x)[kLd] = s_xb[c & 1];
+        float (*s_y)[kLd] = s_yb[c & 1];
         // horizontal: rows [0, kInH) x output columns [0, kTX); lanes take consecutive rows
         for (int it = threadIdx.x; it < kInH * (kTX / kCB); it += kThreads) {
             const int r = it % kInH, q0 = (it / kInH) * kCB;
@@ -175,13 +196,26 @@ __global__ void __launch_bounds__(kThreads) k_ssim_fwd(LossArgs a) {
 
 // Backward: the same blocked passes over the maps A, B, C, then the gradient with the L1 term.
 __global__ void __launch_bounds__(kThreads) k_ssim_bwd(LossArgs a) {
-    __shared__ float s_m[3][kInH][kLd];
-    __shared__ float s_h[3][kInH][kHd];
+    // dynamic shared memory: the three maps' tiles double-buffered over the channels, then the
+    // horizontal pass's outputs
+    extern __shared__ float s_dyn[];
+    float (*s_mb)[3][kInH][kLd] = reinterpret_cast<float (*)[3][kInH][kLd]>(s_dyn);
+    float (*s_h)[kInH][kHd] = reinterpret_cast<float (*)[kInH][kHd]>(s_mb + 2);
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const size_t HW = (size_t)a.W * a.H;
+    for (int k = 0; k < 3; ++k) load_halo_async(a, a.maps + (size_t)k * HW, s_mb[0][k], x0, y0);
+    async_commit();
     for (int c = 0; c < 3; ++c) {
-        for (int k = 0; k < 3; ++k) load_halo(a, a.maps + (size_t)(3 * c + k) * HW, s_m[k], x0, y0);
+        if (c < 2) {  // the next channel's maps load while this one computes
+            for (int k = 0; k < 3; ++k)
+                load_halo_async(a, a.maps + (size_t)(3 * (c + 1) + k) * HW, s_mb[(c + 1) & 1][k], x0, y0);
+            async_commit();
+            async_wait<1>();
+        } else {
+            async_wait<0>();
+        }
         __syncthreads();
+        float (*s_m)[kInH][kLd] = s_mb[c & 1];
         for (int it = threadIdx.x; it < kInH * (kTX / kCB); it += kThreads) {
             const int r = it % kInH, q0 = (it / kInH) * kCB;
             float o[3][kCB];
@@ -322,8 +356,17 @@ extern "C" odgs_status odgs_loss_l1_dssim(const float* image, const float* targe
         return cudaGetLastError() == cudaSuccess ? ODGS_OK : ODGS_ERR_CUDA;
     }
     const dim3 grid((width + kTX - 1) / kTX, (height + kTY - 1) / kTY);
-    k_ssim_fwd<<<grid, kThreads, 0, st>>>(a);
+    constexpr size_t kFwdSmem = sizeof(float) * (4 * kInH * kLd + 5 * kInH * kHd);
+    constexpr size_t kBwdSmem = sizeof(float) * (6 * kInH * kLd + 3 * kInH * kHd);
+    static bool smem_set = false;
+    if (!smem_set) {
+        if (cudaFuncSetAttribute(k_ssim_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_ssim_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem) != cudaSuccess)
+            return ODGS_ERR_CUDA;
+        smem_set = true;
+    }
+    k_ssim_fwd<<<grid, kThreads, kFwdSmem, st>>>(a);
     k_loss_reduce<<<1, kThreads, 0, st>>>(a.partial, blocks_for(width, height), loss, p->accumulate ? 1 : 0);
-    if (grad) k_ssim_bwd<<<grid, kThreads, 0, st>>>(a);
+    if (grad) k_ssim_bwd<<<grid, kThreads, kBwdSmem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? ODGS_OK : ODGS_ERR_CUDA;
 }
