@@ -26,8 +26,9 @@
  *
  * Errors: argument errors are returned synchronously (nothing is launched). CUDA launch errors
  * return ODGS_ERR_CUDA. Errors found on the device (pair capacity exceeded, a bounded wait
- * that gave up) set bits in a device status word: the kernels skip the work they cannot do
- * without writing out of bounds, and odgs_query_pairs / odgs_get_status report the bits.
+ * that gave up, non-finite inputs when odgs_settings.checked is set) set bits in a device
+ * status word: the kernels skip the work they cannot do without writing out of bounds, and
+ * odgs_query_pairs / odgs_get_status report the bits.
  */
 #ifndef ODGS_H
 #define ODGS_H
@@ -45,6 +46,7 @@ typedef enum {
     ODGS_ERR_CAPACITY = -2,    /* more tile/Gaussian pairs than the pair buffer holds          */
     ODGS_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed                  */
     ODGS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up (results are invalid)     */
+    ODGS_ERR_NONFINITE = -5,   /* a non-finite parameter or image gradient (checked mode)      */
     ODGS_ERR_STATE = -6,       /* calls made out of order (e.g. render before bin_sort)        */
     ODGS_ERR_WORKSPACE = -7    /* workspace or pair buffer smaller than required               */
 } odgs_status;
@@ -52,6 +54,8 @@ typedef enum {
 /* Device status word bits, reported by odgs_get_status. */
 #define ODGS_DEV_CAPACITY 1u
 #define ODGS_DEV_TIMEOUT 2u
+#define ODGS_DEV_NONFINITE 4u  /* checked mode: a Gaussian with a non-finite parameter (culled
+                                  in every view) or a non-finite dL/dimage value (taken as 0) */
 
 #define ODGS_MAX_VIEWS 64
 
@@ -96,6 +100,10 @@ typedef struct {
     int pixels_per_thread_bwd; /* backward blend, the same choices; 0 -> 4 if that fits, else the
                                   largest of 4, 2, 1 that does. Per-pixel results do not depend
                                   on either value                                           */
+    int checked;        /* 1: check the Gaussian parameters (after activation) and dL/dimage
+                           for NaN / inf: an offending Gaussian is culled in every view, an
+                           offending gradient value counts as 0, and ODGS_DEV_NONFINITE is set.
+                           0: no checks (non-finite inputs give unspecified results)      */
 } odgs_settings;
 
 /* Gaussian parameters, device pointers, float32, contiguous:

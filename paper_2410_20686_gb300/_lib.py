@@ -11,12 +11,13 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libodgs.so")
 
 ODGS_OK = 0
-ODGS_ERR_INVALID_ARG, ODGS_ERR_CAPACITY, ODGS_ERR_CUDA, ODGS_ERR_TIMEOUT = -1, -2, -3, -4
+ODGS_ERR_INVALID_ARG, ODGS_ERR_CAPACITY, ODGS_ERR_CUDA, ODGS_ERR_TIMEOUT, ODGS_ERR_NONFINITE = -1, -2, -3, -4, -5
 ODGS_ERR_STATE, ODGS_ERR_WORKSPACE = -6, -7
 STATUS_NAMES = {0: "ODGS_OK", -1: "ODGS_ERR_INVALID_ARG", -2: "ODGS_ERR_CAPACITY", -3: "ODGS_ERR_CUDA",
-                -4: "ODGS_ERR_TIMEOUT", -6: "ODGS_ERR_STATE", -7: "ODGS_ERR_WORKSPACE"}
+                -4: "ODGS_ERR_TIMEOUT", -5: "ODGS_ERR_NONFINITE", -6: "ODGS_ERR_STATE", -7: "ODGS_ERR_WORKSPACE"}
 DEV_CAPACITY = 1
 DEV_TIMEOUT = 2
+DEV_NONFINITE = 4
 MAX_VIEWS = 64
 
 # every symbol include/odgs.h declares
@@ -43,7 +44,8 @@ class Settings(C.Structure):
     _fields_ = [("sh_degree", C.c_int), ("sh_coeffs", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int),
                 ("batch", C.c_int), ("cov_dilation", C.c_float), ("r_near", C.c_float), ("r_far", C.c_float),
                 ("bg", C.c_float * 3), ("recompute_lists", C.c_int), ("grad_accumulate", C.c_int),
-                ("pixels_per_thread", C.c_int), ("raw_params", C.c_int), ("pixels_per_thread_bwd", C.c_int)]
+                ("pixels_per_thread", C.c_int), ("raw_params", C.c_int), ("pixels_per_thread_bwd", C.c_int),
+                ("checked", C.c_int)]
 
 
 class Gaussians(C.Structure):

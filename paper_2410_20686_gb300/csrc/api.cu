@@ -104,6 +104,7 @@ odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
     for (int c = 0; c < 3; ++c)
         if (!finite(t.bg[c])) return ODGS_ERR_INVALID_ARG;
     if (t.raw_params != 0 && t.raw_params != 1) return ODGS_ERR_INVALID_ARG;
+    if (t.checked != 0 && t.checked != 1) return ODGS_ERR_INVALID_ARG;
     *out = t;
     return ODGS_OK;
 }
@@ -179,6 +180,7 @@ const char* odgs_status_string(odgs_status st) {
         case ODGS_ERR_CAPACITY: return "pair capacity exceeded";
         case ODGS_ERR_CUDA: return "CUDA error";
         case ODGS_ERR_TIMEOUT: return "device wait timed out";
+        case ODGS_ERR_NONFINITE: return "non-finite input";
         case ODGS_ERR_STATE: return "call out of order";
         case ODGS_ERR_WORKSPACE: return "workspace too small";
     }
@@ -235,6 +237,7 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.st.dilation = c->s.cov_dilation; a.st.r_near = c->s.r_near; a.st.r_far = c->s.r_far;
     for (int i = 0; i < 3; ++i) a.st.bg[i] = c->s.bg[i];
     a.st.raw = c->s.raw_params;
+    a.st.checked = c->s.checked;
     a.rec_a = reinterpret_cast<float4*>(w + c->L.rec_a);
     a.rec_b = reinterpret_cast<float4*>(w + c->L.rec_b);
     a.rec_c = reinterpret_cast<float4*>(w + c->L.rec_c);
@@ -300,6 +303,7 @@ odgs_status odgs_query_pairs(odgs_ctx* c, size_t* pairs, void* stream) {
     *pairs = (size_t)h.pairs;
     if (h.status & kStTimeout) return ODGS_ERR_TIMEOUT;
     if (h.status & kStCapacity) return ODGS_ERR_CAPACITY;
+    if (h.status & kStNonfinite) return ODGS_ERR_NONFINITE;
     return ODGS_OK;
 }
 
@@ -458,6 +462,7 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
     for (int i = 0; i < 3; ++i) a.bg[i] = c->s.bg[i];
     a.acc = acc;
     a.hdr = hdr;
+    a.checked = c->s.checked;
     const int grid = persistent_grid(c, render_bwd_occupancy(c->s.tile_w, c->s.tile_h, a.batch, a.ppt));
     if (launch_render_bwd(a, grid, st) != cudaSuccess) return ODGS_ERR_CUDA;
     c->launches += 1;

@@ -27,6 +27,7 @@ constexpr float kPi = 3.14159265358979323846f;
 // device status bits (mirrors ODGS_DEV_* in odgs.h)
 constexpr uint32_t kStCapacity = 1u;
 constexpr uint32_t kStTimeout = 2u;
+constexpr uint32_t kStNonfinite = 4u;
 
 // Per-view constants, uploaded once per frame into the workspace.
 struct ViewDev {
@@ -79,7 +80,8 @@ struct Settings {
     int tile_w, tile_h;
     float dilation, r_near, r_far;
     float bg[3];
-    int raw;  // scales are log-scales and opacity logits
+    int raw;      // scales are log-scales and opacity logits
+    int checked;  // flag and cull non-finite parameters
 };
 
 // Activation of the raw variables of 3DGS training: scale = exp(log-scale), opacity =

@@ -131,6 +131,7 @@ struct BwdArgs {
     float bg[3];
     float4* acc;
     Header* hdr;
+    int checked;  // flag non-finite dL/dimage values and take them as 0
 };
 
 cudaError_t launch_setup(const ViewTable& tab, ViewDev* views, float4* trig, Header* hdr, int total_trig,

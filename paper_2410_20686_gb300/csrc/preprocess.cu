@@ -231,6 +231,14 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
             s0 = expf(s0); s1 = expf(s1); s2 = expf(s2);
             o = sigmoid_act(o);
         }
+        bool finite_in = true;  // checked mode: a Gaussian with a non-finite parameter is culled
+        if (a.st.checked) {
+            finite_in = isfinite(m0) && isfinite(m1) && isfinite(m2) && isfinite(s0) && isfinite(s1) &&
+                        isfinite(s2) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && isfinite(o);
+            const float* shg = a.sh + (size_t)g * 3 * a.sh_coeffs;
+            for (int k = 0; k < 3 * a.sh_coeffs; ++k) finite_in = finite_in && isfinite(__ldg(shg + k));
+            if (!finite_in) atomicOr(&a.hdr->status, kStNonfinite);
+        }
 
         // Sigma = M M^T with M = R(q) S (Sec. 3.1)
         float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
             uint4 rect = make_uint4(0u, 0u, 0u, 0u);
             uint32_t key = 0xFFFFFFFFu;
             const float r = depth_key(V, m0, m1, m2);
-            bool ok = (r > a.st.r_near) && (r < a.st.r_far) && (Qalpha > 0.f);
+            bool ok = finite_in && (r > a.st.r_near) && (r < a.st.r_far) && (Qalpha > 0.f);
             // camera-space mean in float-float: t = W mu + t_wc
             ff t[3];
 #pragma unroll
@@ -632,7 +640,9 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         }
     }
 
-    if (a.raw) {  // chain through the activations: d/dlog s = d/ds * s, d/dlogit = d/do * o (1 - o)
+    // chain through the activations: d/dlog s = d/ds * s, d/dlogit = d/do * o (1 - o); a Gaussian
+    // that contributed nowhere keeps exact zeros (also when a scale is inf)
+    if (a.raw && any) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) gs[i] *= s[i];
         const float o = sigmoid_act(__ldg(a.opacity + g));

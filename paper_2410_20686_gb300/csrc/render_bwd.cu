@@ -119,6 +119,13 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                 nl[k] = (int)a.n_last[V.pix_base + pix];
                 const float* gi = a.dL_dimages[v];
                 g0[k] = gi[pix]; g1[k] = gi[HW + pix]; g2[k] = gi[2 * HW + pix];
+                if (a.checked) {  // a non-finite gradient value counts as 0 and is reported
+                    const bool f0 = isfinite(g0[k]), f1 = isfinite(g1[k]), f2 = isfinite(g2[k]);
+                    if (!(f0 && f1 && f2)) {
+                        atomicOr(&a.hdr->status, kStNonfinite);
+                        g0[k] = f0 ? g0[k] : 0.f; g1[k] = f1 ? g1[k] : 0.f; g2[k] = f2 ? g2[k] : 0.f;
+                    }
+                }
                 Bg[k] = T[k] * (a.bg[0] * g0[k] + a.bg[1] * g1[k] + a.bg[2] * g2[k]);
                 tmax = max(tmax, nl[k]);
                 evals += (uint32_t)nl[k];

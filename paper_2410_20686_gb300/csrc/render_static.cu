@@ -156,6 +156,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     a.st.dilation = st.cov_dilation; a.st.r_near = st.r_near; a.st.r_far = st.r_far;
     for (int i = 0; i < 3; ++i) a.st.bg[i] = st.bg[i];
     a.st.raw = st.raw_params;
+    a.st.checked = st.checked;
     a.rec_a = rec_a; a.rec_b = rec_b; a.rec_c = rec_c; a.rect = rect; a.rect2 = rect2; a.dkey = dk[0]; a.dval = dv[0];
     a.hdr = hdr;
     if (launch_preprocess(a, st.sh_degree, strm) != cudaSuccess) return ODGS_ERR_CUDA;

@@ -29,6 +29,7 @@ class RenderSettings:
     pixels_per_thread: int = 0      # forward blend (0: automatic, 2 where it fits)
     raw_params: bool = False  # scales are log-scales and opacity logits (activated by the kernels)
     pixels_per_thread_bwd: int = 0  # backward blend (0: automatic, 4 where it fits)
+    checked: bool = False  # flag (ODGS_DEV_NONFINITE) and cull non-finite parameters / gradients
 
     def c_struct(self, sh_coeffs: int) -> L.Settings:
         s = L.Settings()
@@ -41,6 +42,7 @@ class RenderSettings:
         s.pixels_per_thread = int(self.pixels_per_thread)
         s.raw_params = int(bool(self.raw_params))
         s.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
+        s.checked = int(bool(self.checked))
         return s
 
 
@@ -156,7 +158,8 @@ class Rasterizer:
         p = C.c_size_t()
         stream = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
         st = self.lib.odgs_query_pairs(self.ctx, C.byref(p), stream)
-        if st not in (L.ODGS_OK, -2):
+        # capacity and non-finite inputs are reported by status() and do not stop the frame
+        if st not in (L.ODGS_OK, L.ODGS_ERR_CAPACITY, L.ODGS_ERR_NONFINITE):
             L.check(st, "odgs_query_pairs")
         return int(p.value)
 

@@ -98,3 +98,21 @@ def test_null_context_rejected(lib):
     assert lib.odgs_preprocess_bwd(None, None, None) == -1
     assert lib.odgs_create(None) == -1
     assert lib.odgs_status_string(-2).decode() == "pair capacity exceeded"
+
+
+def test_status_codes_and_device_bits_agree_with_the_header():
+    text = open(os.path.join(ROOT, "include", "odgs.h")).read()
+    codes = dict((n, int(v)) for n, v in re.findall(r"\b(ODGS_(?:OK|ERR_[A-Z_]+))\s*=\s*(-?\d+)", text))
+    for name, value in codes.items():
+        assert getattr(L, name) == value, name
+        assert L.STATUS_NAMES[value] == name
+    bits = dict((n, int(v)) for n, v in re.findall(r"#define ODGS_DEV_([A-Z_]+) (\d+)u", text))
+    assert bits == {"CAPACITY": L.DEV_CAPACITY, "TIMEOUT": L.DEV_TIMEOUT, "NONFINITE": L.DEV_NONFINITE}
+
+
+def test_checked_setting_is_validated(lib):
+    views = _views((256, 128))
+    st, _ = _ws(lib, 100, views, 1, _settings(checked=2))
+    assert st == L.ODGS_ERR_INVALID_ARG
+    st, _ = _ws(lib, 100, views, 1, _settings(checked=1))
+    assert st == L.ODGS_OK
