@@ -1,6 +1,7 @@
 // Backward alpha blending (reverse of Eq. 3) on ERP tiles (sm_103a).
 //
-// Same persistent (view, tile) schedule and PPT-pixels-per-thread layout as the forward kernel.
+// Same persistent (view, tile) schedule and layout as the forward kernel: PPT pixels of one row per
+// thread, tile_w / PPT columns apart.
 // Each pixel starts from its final transmittance and the index after its last blended Gaussian,
 // and walks its tile list back to front, recovering T_j = T_{j+1} / (1 - alpha_j). Per blended
 // Gaussian it forms
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int tw = a.tile_w;
     const int tpr = tw / PPT;
-    const int lx0 = (tid % tpr) * PPT, ly = tid / tpr;
+    // a thread's PPT pixels are tpr columns apart (interleaved), so a footprint a few pixels wide
+    // falls in one of each lane's pixel slots rather than in several
+    const int lx0 = tid % tpr, ly = tid / tpr;
     const int wy0 = (warp << 5) / tpr, wy1 = ((warp << 5) + 31) / tpr;  // the warp's tile rows
     uint32_t evals = 0u;
 
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
         for (int k = 0; k < PPT; ++k) {
             T[k] = 1.f; Bg[k] = 0.f; g0[k] = g1[k] = g2[k] = 0.f; nl[k] = 0;
             if (inside) {
-                const int pix = y * V.W + xp + k;
+                const int pix = y * V.W + xp + k * tpr;
                 const int HW = V.W * V.H;
                 T[k] = a.T_final[V.pix_base + pix];
                 nl[k] = (int)a.n_last[V.pix_base + pix];
@@ -180,14 +183,14 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                     if (!any_split) {
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
-                            dxk[k] = __fsub_rn(__fsub_rn(fi0 + (float)k, P.x), P.z);
+                            dxk[k] = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), P.z);
                             pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
                         }
                     } else {
                         const float fsplit = s_col[j].w, fc2 = s_fc2[j];
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
-                            const float fi = fi0 + (float)k;
+                            const float fi = fi0 + (float)(k * tpr);
                             dxk[k] = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), P.z);
                             pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
                         }

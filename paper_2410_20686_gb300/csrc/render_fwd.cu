@@ -6,7 +6,7 @@
 // tile's staged form (seam shift, base-2 conic, log2 opacity) in shared memory, then evaluate the
 // batch from shared memory (broadcast reads).
 //
-// Each thread owns PPT consecutive pixels of one row. The row-constant part of Eq. 2's quadratic
+// Each thread owns PPT pixels of one row, tile_w / PPT columns apart. The row-constant part of Eq. 2's quadratic
 // form (B dy and C dy^2 + log2 o) and the shared-memory loads are paid once per thread and entry,
 // not once per pixel; the kernel is bound by instruction issue, so this is where its time goes.
 // A pixel stops before the Gaussian that would take its transmittance below 1e-4; a thread stops
@@ -35,7 +35,9 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int tw = a.tile_w;
     const int tpr = tw / PPT;  // threads per pixel row
-    const int lx0 = (tid % tpr) * PPT, ly = tid / tpr;
+    // a thread's PPT pixels are tpr columns apart (interleaved), so a footprint a few pixels wide
+    // falls in one of each lane's pixel slots rather than in several
+    const int lx0 = tid % tpr, ly = tid / tpr;
     uint32_t evals = 0u, blended = 0u;  // (pixel, entry) evaluations / blends by this thread
     unsigned long long etile = 0ull;    // thread 0: sum of s_etile over this CTA's tiles
     if (tid == 0) s_etile = 0u;
@@ -97,14 +99,14 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
                 if (!any_split) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float dx = __fsub_rn(__fsub_rn(fi0 + (float)k, P.x), P.z);
+                        const float dx = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), P.z);
                         pk[k] = __fmaf_rn(__fmaf_rn(K.x, dx, Bdy), dx, rr);
                     }
                 } else {
                     const float fsplit = s_col[j].w, fc2 = s_fc2[j];
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float fi = fi0 + (float)k;
+                        const float fi = fi0 + (float)(k * tpr);
                         const float dx = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), P.z);
                         pk[k] = __fmaf_rn(__fmaf_rn(K.x, dx, Bdy), dx, rr);
                     }
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
             float* img = a.images[v];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                const int pix = y * V.W + xp + k;
+                const int pix = y * V.W + xp + k * tpr;
                 img[pix] = __fmaf_rn(T[k], a.bg[0], C0[k]);
                 img[HW + pix] = __fmaf_rn(T[k], a.bg[1], C1[k]);
                 img[2 * HW + pix] = __fmaf_rn(T[k], a.bg[2], C2[k]);
