@@ -513,6 +513,7 @@ def run_ours(args):
 
     from paper_2410_20686_gb300 import build as B
     from paper_2410_20686_gb300 import scenes as S
+    from paper_2410_20686_gb300.graph import GraphedFrame
     from paper_2410_20686_gb300.loss import l1_dssim
     from paper_2410_20686_gb300.rasterizer import Rasterizer, RenderSettings
 
@@ -572,7 +573,6 @@ def run_ours(args):
     rast.capacity_mode = "fixed"
     stats = rast.stats()
     assert stats["status"] == 0, stats
-    launches_per_step = rast.launch_count()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -583,7 +583,23 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     K = args.steps
+    # per-stage times: an eager run of the step with CUDA events between the stages
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    for i in range(K):
+        step(evs[i])
+    torch.cuda.synchronize()
+    stats = rast.stats()
+    assert stats["status"] == 0, stats
+    names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
+    kern = {nm: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)])) for j, nm in enumerate(names)}
+    eager_ms = float(np.mean([evs[i][0].elapsed_time(evs[i][6]) for i in range(K)]))
+
+    # the timed steps: the same fwd+bwd step (same kernels, inputs and fused L1 loss) replayed from a
+    # CUDA graph, as a training loop runs it (GraphedFrame), which removes the host launch gaps
+    frames = [GraphedFrame(params, [view], [target], rs)]
+    for _ in range(args.warmup):
+        frames[0].replay()
+    torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(_gpu_id(torch, local))
     barrier()
@@ -591,26 +607,25 @@ def run_ours(args):
     sampler.start()
     start.record()
     for i in range(K):
-        step(evs[i])
+        frames[0].replay()
     stop.record()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
     elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3, world, dev)
-    stats = rast.stats()
-    assert stats["status"] == 0, stats
-
-    names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
-    kern = {nm: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(K)])) for j, nm in enumerate(names)}
+    assert frames[0].status() == 0
+    graph_launches = frames[0].launches
 
     # end-to-end through host buffers: every step copies its parameters and target in from pinned
-    # host memory and reads its loss back. The copies run on a second stream into one of two device
-    # input sets, so step i+1's upload overlaps step i's kernels (a data loader's prefetch); the
-    # first upload and the last loss read are inside the timed region.
+    # host memory and reads its loss back. The copies run on a second stream into the inputs of one
+    # of two graphed frames, so step i+1's upload overlaps step i's kernels (a data loader's
+    # prefetch); the first upload and the last loss read are inside the timed region.
     e2e = None
     if not args.no_e2e:
         host = [t_.cpu().pin_memory() for t_ in params] + [target.cpu().pin_memory()]
-        sets = [params + [target], [torch.empty_like(h, device=dev) for h in host]]
+        second = [t_.clone() for t_ in params]
+        frames.append(GraphedFrame(second, [view], [target.clone()], rs))
+        sets = [f.params + f.targets for f in frames]
         h2d = sum(h.numel() * h.element_size() for h in host)
         copy_stream = torch.cuda.Stream(dev)
         main = torch.cuda.current_stream(dev)
@@ -636,9 +651,9 @@ def run_ours(args):
                 if i + 1 < steps:
                     upload(1 - j)
                 main.wait_event(loaded[j])
-                loss = step(inputs=sets[j])
+                loss = frames[j].replay()
                 freed[j].record(main)
-                loss_host[j].copy_(loss, non_blocking=True)
+                loss_host[j].copy_(loss.reshape(()), non_blocking=True)
                 read[j].record(main)
                 if i > 0:  # the previous step's loss, read while this step runs
                     read[1 - j].synchronize()
@@ -655,8 +670,10 @@ def run_ours(args):
         barrier()
         te = max_over_ranks(time.perf_counter() - t0, world, dev)
         assert len(losses) == K and all(np.isfinite(losses)), losses
+        assert all(f.status() == 0 for f in frames)
         e2e = {"value": job_rate(world, K, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
-               "overlap": "uploads on a second stream, double-buffered; losses read one step behind"}
+               "overlap": "uploads on a second stream into the inputs of two graphed frames; losses read one "
+                          "step behind"}
 
     if rank != 0:
         if world > 1:
@@ -690,8 +707,11 @@ def run_ours(args):
                       "sh_degree": 3, "tile": args.tile, "batch": args.batch, "pixels_per_thread": args.ppt,
                       "pixels_per_thread_bwd": args.ppt_bwd,
                       "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
+                      "timing": "whole fwd+bwd step replayed from a CUDA graph (GraphedFrame), CUDA events around "
+                                "K replays; kernels_ms from an eager run with events between the stages",
                       "parallelism": f"replicas x{world}"},
-           "roofline": roofline, "kernels_ms": kern, "kernels": kernels, "gpu_launches": launches_per_step * K,
+           "roofline": roofline, "kernels_ms": kern, "kernels": kernels, "gpu_launches": graph_launches * K,
+           "eager_ms_per_step": eager_ms,
            "clocks": clocks}
     if e2e:
         out["e2e"] = e2e
