@@ -194,8 +194,8 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
 # bench reports null until it is captured again.
 PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh"),
                     "structs": ("odgs_internal.h", "BwdArgs"),
-                    "sha256": "d515b59e471727ea848455de5a523ba1e555d9677748c228a2a592e2f5db15ba",
-                    "bytes": 175064832}
+                    "sha256": "2dad9b09eb4717a4d99e627196ad2d7fb6b7459520237758b9eb13fc248b99a8",
+                    "bytes": 174502400}
 
 
 def kernel_sources_digest(spec=PROFILED_TRAFFIC):
