@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the forward blend (0 = auto)")
     ap.add_argument("--ppt-bwd", type=int, default=0, help="pixels per thread in the backward blend (0 = auto)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view batched measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 8 x 4096x2048 roaming-scale measurement")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-next", action="store_true", help="skip the measurements of the steps after the hot path")
     return ap.parse_args()
@@ -350,6 +351,53 @@ def run_batched(dev, rs, steps, warmup):
     return {"workload": BATCHED_WORKLOAD, "views_per_s": V / t_b, "single_views_per_s": V / t_s,
             "speedup": t_s / t_b, "ms_per_frame": t_b * 1e3, "ms_per_views_one_at_a_time": t_s * 1e3,
             "kernel_launches_per_frame": gf.launches, "steps": steps, "per_gpu": True}
+
+
+LARGE_WORKLOAD = ("config4: 3,000,000 Gaussians (SH3) along a 50 m corridor (30% in 100 clusters), 8 ERP views "
+                  "of 4096x2048 every 6 m, fwd+bwd with L1 loss, gradients of all views summed into one buffer")
+
+
+def run_batched_large(dev, rs, steps, warmup, group_size=2):
+    """views/s of the roaming-scale frame: GroupedFrame (groups of views sharing one pair buffer,
+    tile lists rebuilt in each group's backward pass, as the configuration prescribes), and for
+    comparison all 8 views in one CUDA-graph-replayed frame with the lists kept."""
+    import torch
+    from paper_2410_20686_gb300 import scenes as S
+    from paper_2410_20686_gb300.graph import GraphedFrame, GroupedFrame
+
+    sc = S.config4()
+    params = [torch.tensor(a, device=dev) for a in (sc.means, sc.scales, sc.quats, sc.opacity, sc.sh)]
+    targets = [torch.tensor(t, device=dev) for t in S.target_images(sc, 4)]
+    V = len(sc.views)
+    px = sum(v.width * v.height for v in sc.views)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    grouped = GroupedFrame(params, sc.views, targets, rs, group_size=group_size)
+    t_g = timed(grouped.step)
+    assert grouped.status() == 0
+    pair_bytes = grouped.pair_buffer_bytes()
+    del grouped
+    torch.cuda.empty_cache()
+    whole = GraphedFrame(params, sc.views, targets, rs)
+    t_w = timed(whole.replay)
+    assert whole.status() == 0
+    whole_pairs = whole.rast.stats()["pairs"]
+    return {"workload": LARGE_WORKLOAD, "views_per_s": V / t_g, "ms_per_frame": t_g * 1e3,
+            "pixels_per_s": px / t_g, "mode": f"GroupedFrame, {group_size} views per group, lists rebuilt in "
+                                              f"the backward pass", "pair_buffer_bytes": pair_bytes,
+            "all_views_graphed": {"views_per_s": V / t_w, "ms_per_frame": t_w * 1e3, "pairs": whole_pairs},
+            "steps": steps, "per_gpu": True}
 
 
 # ------------------------------------------------------------------ densification (Sec. 3.3)
@@ -717,6 +765,8 @@ def run_ours(args):
         out["e2e"] = e2e
     if not args.no_batched:
         out["batched"] = run_batched(dev, rs, args.batched_steps, args.warmup)
+    if not args.no_large:
+        out["batched_large"] = run_batched_large(dev, rs, steps=5, warmup=2)
     if not args.no_next:
         imgs_last, _ = rast.forward(*params, [view], rs, want_T=False)
         imgs_last = imgs_last[0]
