@@ -11,10 +11,12 @@
 // (zero when alpha was clamped at 0.99). The skip / clamp decisions and alpha are recomputed
 // with the forward kernel's exact operation sequence, so they match it bit for bit.
 //
-// A thread first sums the nine values over its PPT pixels; the warp then sums them over its
-// lanes with a transpose reduction (12 shuffles for 9 values), the CTA over its warps in shared
-// memory, and the result is added to the per-(view, Gaussian) accumulator with three 16-byte
-// vector atomics. A warp whose pixels all stopped before an entry skips it, and so does a warp
+// A thread first sums nine values over its PPT pixels: dL/drgb and, with dp = dL/d(power), the
+// sums of dp, dp dx, dp dx^2, and dy times the first two and dy^2 times the first (dy is the
+// same for all of a thread's pixels). The warp sums them over its lanes with a transpose
+// reduction (12 shuffles for 9 values), the CTA over its warps in shared memory; then one thread
+// per entry forms dL/d(u, v, conic, opacity), which are linear in these sums, and adds them to the
+// per-(view, Gaussian) accumulator with three 16-byte vector atomics. A warp whose pixels all stopped before an entry skips it, and so does a warp
 // none of whose pixel rows lies within the entry's footprint rows (the rows the binning lists the
 // Gaussian in; outside them no pixel reaches alpha = 1/255); a warp with a single contributing
 // lane skips the reduction.
@@ -195,49 +197,42 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                             pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
                         }
                     }
-                    bool any = false;
+                    const float4 c = s_col[j];
+                    // sums over this thread's pixels of dp, dp dx and dp dx^2 (dp = dL/d power); the
+                    // conic, opacity and mean terms are linear in these sums and in dy times them,
+                    // so the warp reduces the sums and the CTA pass after the batch forms the terms
+                    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) any |= (e < nl[k]) & (pk[k] >= kLog2AlphaMin);
-                    if (any) {
+                    for (int k = 0; k < PPT; ++k) {
+                        if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
                         contrib = true;
-                        const float4 c = s_col[j];
-                        const float4 R = s_raw[j];
-                        // sums over this thread's pixels of dp, dp dx and dp dx^2 (dp = dL/d power);
-                        // the conic, opacity and mean terms follow from them once per entry, as dy
-                        // is the same for all of the thread's pixels
-                        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
-#pragma unroll
-                        for (int k = 0; k < PPT; ++k) {
-                            if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
-                            const float dx = dxk[k];
-                            const float ar = alpha_exp2(pk[k]);
-                            const float alpha = fminf(kAlphaMax, ar);
-                            const float inv = __fdividef(1.f, __fsub_rn(1.f, alpha));
-                            const float Tj = T[k] * inv;
-                            const float w = alpha * Tj;
-                            const float cg = c.x * g0[k] + c.y * g1[k] + c.z * g2[k];
-                            vals[6] += w * g0[k];
-                            vals[7] += w * g1[k];
-                            vals[8] += w * g2[k];
-                            const float dLda = Tj * cg - Bg[k] * inv;
-                            Bg[k] = fmaf(cg, w, Bg[k]);
-                            T[k] = Tj;
-                            if (ar < kAlphaMax) {  // no gradient through the 0.99 clamp
-                                const float dp = dLda * alpha;  // dL/d(power), power = ln G
-                                const float dpx = dp * dx;
-                                S0 += dp;
-                                S1 += dpx;
-                                S2 = fmaf(dpx, dx, S2);
-                            }
+                        const float dx = dxk[k];
+                        const float ar = alpha_exp2(pk[k]);
+                        const float alpha = fminf(kAlphaMax, ar);
+                        const float inv = __fdividef(1.f, __fsub_rn(1.f, alpha));
+                        const float Tj = T[k] * inv;
+                        const float w = alpha * Tj;
+                        const float cg = c.x * g0[k] + c.y * g1[k] + c.z * g2[k];
+                        vals[6] += w * g0[k];
+                        vals[7] += w * g1[k];
+                        vals[8] += w * g2[k];
+                        const float dLda = Tj * cg - Bg[k] * inv;
+                        Bg[k] = fmaf(cg, w, Bg[k]);
+                        T[k] = Tj;
+                        if (ar < kAlphaMax) {  // no gradient through the 0.99 clamp
+                            const float dp = dLda * alpha;  // dL/d(power), power = ln G
+                            const float dpx = dp * dx;
+                            S0 += dp;
+                            S1 += dpx;
+                            S2 = fmaf(dpx, dx, S2);
                         }
-                        // power = ln o - (a dx^2 + 2 b dx dy + c dy^2) / 2 with (dx, dy) = pixel - mean
-                        vals[5] = S0 * R.w;
-                        vals[2] = -0.5f * S2;
-                        vals[3] = -dy * S1;
-                        vals[4] = (-0.5f * dy * dy) * S0;
-                        vals[0] = R.x * S1 + (R.y * dy) * S0;
-                        vals[1] = R.y * S1 + (R.z * dy) * S0;
                     }
+                    vals[0] = S0;
+                    vals[1] = S1;
+                    vals[2] = S2;
+                    vals[3] = dy * S0;
+                    vals[4] = dy * S1;
+                    vals[5] = dy * vals[3];
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, contrib);
                 if (m == 0u) {
@@ -255,16 +250,26 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                 }
             }
             __syncthreads();
-            for (int q = tid; q < cnt * 3; q += nthr) {
-                const int jj = q / 3, part = q - 3 * jj;
-                const int nv = part < 2 ? 4 : 1;
-                float sum[4] = {0.f, 0.f, 0.f, 0.f};
+            // per entry: the warps' sums added, then the screen-space gradient terms. With (dx, dy) =
+            // pixel - mean, power = ln o - (a dx^2 + 2 b dx dy + c dy^2) / 2, so
+            //   dL/du = a S1 + b (dy S0), dL/dv = b S1 + c (dy S0), dL/da = -S2 / 2,
+            //   dL/db = -(dy S1), dL/dc = -(dy^2 S0) / 2, dL/do = S0 / o
+            for (int jj = tid; jj < cnt; jj += nthr) {
+                float q[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) q[k] = 0.f;
                 for (int w = 0; w < nwarps; ++w) {
-                    const float* r = s_red + ((size_t)jj * nwarps + w) * 9 + 4 * part;
-                    for (int k = 0; k < nv; ++k) sum[k] += r[k];
+                    const float* r = s_red + ((size_t)jj * nwarps + w) * 9;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) q[k] += r[k];
                 }
-                if (sum[0] != 0.f || sum[1] != 0.f || sum[2] != 0.f || sum[3] != 0.f)
-                    red_add_v4(a.acc + 3 * (size_t)s_idx[jj] + part, make_float4(sum[0], sum[1], sum[2], sum[3]));
+                const float4 R = s_raw[jj];
+                const float4 p0 = make_float4(R.x * q[1] + R.y * q[3], R.y * q[1] + R.z * q[3], -0.5f * q[2], -q[4]);
+                const float4 p1 = make_float4(-0.5f * q[5], R.w * q[0], q[6], q[7]);
+                float4* dst = a.acc + 3 * (size_t)s_idx[jj];
+                if (p0.x != 0.f || p0.y != 0.f || p0.z != 0.f || p0.w != 0.f) red_add_v4(dst, p0);
+                if (p1.x != 0.f || p1.y != 0.f || p1.z != 0.f || p1.w != 0.f) red_add_v4(dst + 1, p1);
+                if (q[8] != 0.f) red_add_v4(dst + 2, make_float4(q[8], 0.f, 0.f, 0.f));
             }
             __syncthreads();  // the next batch overwrites the staged entries and s_red
         }
