@@ -195,8 +195,8 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
 # bench reports null until it is captured again.
 PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh"),
                     "structs": ("odgs_internal.h", "BwdArgs"),
-                    "sha256": "2dad9b09eb4717a4d99e627196ad2d7fb6b7459520237758b9eb13fc248b99a8",
-                    "bytes": 174502400}
+                    "sha256": "6dbdcdde91622ad219c79f8fc23ce82453e9fa758de767749c0052f4cb5c961d",
+                    "bytes": 170656256}
 
 
 def kernel_sources_digest(spec=PROFILED_TRAFFIC):
