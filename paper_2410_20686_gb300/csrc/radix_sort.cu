@@ -18,8 +18,8 @@ namespace odgs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItemsMax = 16;  // 4096 keys per CTA for large sorts, 2048 below kLargeSort
-constexpr size_t kLargeSort = 4u << 20;
+constexpr int kSortItemsMax = 16;  // 4096 keys per CTA for sorts of at least kLargeSort keys, else 2048
+constexpr size_t kLargeSort = 1u << 19;  // measured: the 1M-item depth sort is faster with 4096-key tiles
 constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
