@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000, help="Gaussians (headline: 1M)")
     ap.add_argument("--width", type=int, default=2048)
     ap.add_argument("--tile", type=str, default="16x16")
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--ppt", type=int, default=0, help="pixels per thread in the forward blend (0 = auto)")
     ap.add_argument("--ppt-bwd", type=int, default=0, help="pixels per thread in the backward blend (0 = auto)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-view batched measurement")

@@ -81,7 +81,8 @@ typedef struct {
     int sh_coeffs;      /* coefficients stored per Gaussian in sh (>= (deg+1)^2)        */
     int tile_w, tile_h; /* pixel tile; 0 -> 16 x 16. tile_w * tile_h in [32, 1024],
                            tile_w in {8, 16, 32}                                       */
-    int batch;          /* Gaussians staged per shared-memory batch; 0 -> 64 (<= 256)   */
+    int batch;          /* Gaussians staged per shared-memory batch by the forward blend;
+                           0 -> 128 (<= 256); the backward stages min(batch, 64)         */
     float cov_dilation; /* added to both diagonals of Sigma_2D (px^2); e.g. 0.3          */
     float r_near, r_far;/* spherical-shell culling radii (Sec. 3.2); e.g. 0.2, 1e4       */
     float bg[3];        /* background colour blended with the final transmittance        */

@@ -97,7 +97,7 @@ odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
     t.pixels_per_thread = pixels_per_thread(t.tile_w, t.tile_h, t.pixels_per_thread, 2);
     t.pixels_per_thread_bwd = pixels_per_thread(t.tile_w, t.tile_h, t.pixels_per_thread_bwd, 4);
     if (t.pixels_per_thread == 0 || t.pixels_per_thread_bwd == 0) return ODGS_ERR_INVALID_ARG;
-    if (t.batch == 0) t.batch = 64;
+    if (t.batch == 0) t.batch = 128;
     if (t.batch < 1 || t.batch > 256) return ODGS_ERR_INVALID_ARG;
     if (!finite(t.cov_dilation) || t.cov_dilation < 0.f) return ODGS_ERR_INVALID_ARG;
     if (!finite(t.r_near) || !(t.r_far > t.r_near) || t.r_near < 0.f) return ODGS_ERR_INVALID_ARG;

@@ -65,7 +65,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     if (g->n > 0 && reinterpret_cast<uintptr_t>(g->quats) % 16 != 0) return ODGS_ERR_INVALID_ARG;
     odgs_settings st = *s;
     if (st.tile_w == 0 && st.tile_h == 0) { st.tile_w = 16; st.tile_h = 16; }
-    if (st.batch == 0) st.batch = 64;
+    if (st.batch == 0) st.batch = 128;
     if (st.sh_degree < 0 || st.sh_degree > 3 || st.sh_coeffs < (st.sh_degree + 1) * (st.sh_degree + 1) ||
         st.sh_coeffs > 64)
         return ODGS_ERR_INVALID_ARG;

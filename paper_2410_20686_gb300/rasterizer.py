@@ -19,7 +19,7 @@ class RenderSettings:
     sh_degree: int = 3
     tile_w: int = 16
     tile_h: int = 16
-    batch: int = 64
+    batch: int = 128  # forward staging batch (the backward stages at most 64)
     cov_dilation: float = 0.3
     r_near: float = 0.2
     r_far: float = 1e4
