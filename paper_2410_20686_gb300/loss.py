@@ -29,7 +29,7 @@ def l1_dssim(images, targets, lam: float = 0.2, area_weight: bool = True, wrap_u
         L.check(lib.odgs_loss_scratch_size(int(im.shape[2]), int(im.shape[1]), C.byref(n)), "odgs_loss_scratch_size")
         need = max(need, int(n.value))
     scratch = torch.empty(need, dtype=torch.uint8, device=dev)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)  # the first view writes it, the others add
     grads = []
     stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     for k, (im, tg) in enumerate(zip(images, targets)):
