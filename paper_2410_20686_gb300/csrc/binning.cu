@@ -1,15 +1,17 @@
 // Tile binning of the depth-sorted items (sm_103a):
-//   k_count_blocks  per block of 2048 depth-sorted items: number of (tile, item) pairs
+//   k_count_blocks  per block of 512 depth-sorted items: number of (tile, item) pairs
 //   k_scan_blocks   exclusive scan of the block totals (one CTA) + capacity check
-//   k_emit          each item writes one (tile id, item) pair per tile of its rectangle, in
-//                   depth order, at its exclusive-scan offset; pairs beyond the capacity are
-//                   dropped (status bit kStCapacity set by k_scan_blocks)
+//   k_emit          each item writes one (tile id, item) pair per tile its footprint meets, in
+//                   depth order, at its exclusive-scan offset, and counts the tile sort's digits;
+//                   items with more than 32 pairs are queued for k_emit_big; pairs beyond the
+//                   capacity are dropped (status bit kStCapacity set by k_scan_blocks)
+//   k_emit_big      the queued items, one warp each
 //   k_tile_ranges   [start, end) of every tile's run in the tile-sorted pair list
-// An item's rect is (ty0 | nty << 16, number of tiles); the tiles of each of its tile rows are
-// recomputed from its records by band_columns (odgs_common.cuh), exactly as the preprocess
-// counted them. Emission is warp-cooperative: a lane writes the pairs of its own item when it has
-// at most 32 of them, and the whole warp writes the pairs of larger items (pole-stretched
-// Gaussians can cover hundreds of tiles), 32 consecutive columns at a time.
+// An item's rect is (ty0 | bands << 16, number of tiles, spans of bands 0 and 1), rect2 the spans
+// of bands 2..5; the columns of further bands are recomputed from its records by band_columns
+// (odgs_common.cuh), exactly as the preprocess counted them. A big item's pairs over its stored
+// bands are one flat range that the warp writes 32 at a time; pole-stretched Gaussians can cover
+// hundreds of tiles.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
