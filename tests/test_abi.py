@@ -116,3 +116,11 @@ def test_checked_setting_is_validated(lib):
     assert st == L.ODGS_ERR_INVALID_ARG
     st, _ = _ws(lib, 100, views, 1, _settings(checked=1))
     assert st == L.ODGS_OK
+
+
+def test_view_size_limits(lib):
+    s = _settings()
+    assert _ws(lib, 100, _views((16384, 8192)), 1, s)[0] == L.ODGS_OK
+    assert _ws(lib, 100, _views((16400, 8192)), 1, s)[0] == L.ODGS_ERR_INVALID_ARG
+    assert _ws(lib, 100, _views((256, 16385)), 1, s)[0] == L.ODGS_ERR_INVALID_ARG
+    assert _ws(lib, 100, _views((250, 128)), 1, s)[0] == L.ODGS_ERR_INVALID_ARG  # not a multiple of the tile width

@@ -143,3 +143,23 @@ def test_config2_sampled_pixels():
     col, T, nc, margins = O.render(O.Params.of(sc), v, oracle_settings(rs), pix=pix)
     gpu = imgs[0].reshape(3, -1)[:, pix].T
     compare_image(gpu, col, margins)
+
+
+def test_largest_view_16384x8192():
+    """The largest supported view: pixel anchors up to 16383 in their 16-bit fields and 524,288
+    tiles. Sampled pixels: random ones, the seam and pole tiles, and the tiles holding the first
+    Gaussians' centres."""
+    sc = S.random_scene(5000, 16384, 8192, seed=23, sh_degree=1, radius=(0.5, 3.0), log_scale=(-3.0, 0.5))
+    rs = _rs(sh_degree=1)
+    imgs, _, _ = gpu_render(sc, rs, want_T=False)
+    v = sc.views[0]
+    p = O.Params.of(sc)
+    st = oracle_settings(rs)
+    pj = O.project(p, v, st)
+    vis = pj[:, O.PJ_VALID] > 0
+    centres = [(int(u) // 16, int(w) // 16) for u, w in pj[vis][:12, [O.PJ_U, O.PJ_V]]]
+    pix = S.sample_pixels(v.width, v.height, 4096, S.stress_tiles(v.width, v.height) + centres, seed=24)
+    col, T, nc, margins = O.render(p, v, st, pix=pix)
+    gpu = imgs[0].reshape(3, -1)[:, pix].T
+    compare_image(gpu, col, margins)
+    assert (nc > 0).sum() > 1000  # the sample reaches many covered pixels, not only background
