@@ -7,7 +7,7 @@
 //
 // One histogram kernel counts the digits of all passes in a single read of the keys; each
 // pass is then one "onesweep" kernel (Adinets & Merrill 2022): a CTA ranks a 2048- or 4096-key
-// tile in shared memory (warp-level match ranking keeps it stable), publishes its per-digit counts,
+// tile in shared memory (warp-level ranking by ballots or a match keeps it stable), publishes its per-digit counts,
 // obtains the exclusive prefix of all earlier tiles by decoupled look-back, and writes its keys
 // digit-run by digit-run (coalesced). Look-back waits are bounded: a CTA that gives up sets
 // kStTimeout in the status word and returns.
@@ -88,7 +88,7 @@ template <int kSortItems>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          const uint32_t* __restrict__ n_ptr, int shift,
-                                                         int bits, const uint32_t* __restrict__ hist,
+                                                         int bits, int use_match, const uint32_t* __restrict__ hist,
                                                          uint32_t* lookback, uint32_t* tile_ctr, uint32_t* status) {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_warp_hist[kSortWarps][kRadix];
@@ -118,15 +118,29 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint32_t* __
         key[i] = valid ? kin[idx] : 0u;
         val[i] = valid ? vin[idx] : 0u;
     }
-    // stable warp-level ranking: items are ordered by (warp, i, lane). The lanes holding the
-    // same digit are found with one warp match (measured faster than a ballot per digit bit).
+    // stable warp-level ranking: items are ordered by (warp, i, lane).
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
         const bool valid = idx < n;
         const uint32_t d = (key[i] >> shift) & mask;
-        // lanes holding the same digit (an invalid lane matches only itself)
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u | (uint32_t)lane));
+        // lanes holding the same digit: a warp match costs more the more distinct digits the warp
+        // holds, so it ranks the last (most significant) pass, where they are few; the others
+        // take one ballot per digit bit (an invalid lane's peers are never used)
+        uint32_t peers;
+        if (use_match) {
+            peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u | (uint32_t)lane));
+        } else {
+            peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                if (b < bits) {
+                    const bool bit = (d >> b) & 1u;
+                    const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                    peers &= bit ? bb : ~bb;
+                }
+            }
+        }
         const uint32_t before = valid ? s_warp_hist[warp][d] : 0u;
         __syncwarp();
         if (valid && lane == (uint32_t)(__ffs(peers) - 1)) s_warp_hist[warp][d] = before + (uint32_t)__popc(peers);
@@ -253,12 +267,12 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
         if ((e = cudaMemsetAsync(lookback, 0, sizeof(uint32_t) * lb_words, st)) != cudaSuccess) return e;
         if (large)
             k_onesweep<kSortItemsMax><<<max(tiles, 1), kSortThreads, 0, st>>>(
-                k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, hist + p * kRadix, lookback,
-                tile_ctrs + p, status);
+                k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
+                hist + p * kRadix, lookback, tile_ctrs + p, status);
         else
             k_onesweep<kSortItemsMax / 2><<<max(tiles, 1), kSortThreads, 0, st>>>(
-                k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, hist + p * kRadix, lookback,
-                tile_ctrs + p, status);
+                k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
+                hist + p * kRadix, lookback, tile_ctrs + p, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
         cur ^= 1;
