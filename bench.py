@@ -350,7 +350,8 @@ def run_batched(dev, rs, steps, warmup):
     assert rast.status() == 0
     return {"workload": BATCHED_WORKLOAD, "views_per_s": V / t_b, "single_views_per_s": V / t_s,
             "speedup": t_s / t_b, "ms_per_frame": t_b * 1e3, "ms_per_views_one_at_a_time": t_s * 1e3,
-            "kernel_launches_per_frame": gf.launches, "steps": steps, "per_gpu": True}
+            "kernel_launches_per_frame": gf.launches + 2 * V, "rasterizer_launches_per_frame": gf.launches,
+            "steps": steps, "per_gpu": True}
 
 
 LARGE_WORKLOAD = ("config4: 3,000,000 Gaussians (SH3) along a 50 m corridor (30% in 100 clusters), 8 ERP views "
