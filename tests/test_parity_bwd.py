@@ -135,3 +135,38 @@ def test_gradients_config1_sampled_loss():
     full[:, pix] = gp.T
     gpu = _gpu_grads(sc, rs, [full.reshape(3, v.height, v.width)])
     _assert_close(gpu, ref)
+
+
+def test_gradients_largest_view_16384x8192():
+    """Backward at the largest supported view (pixel anchors up to 16383 in their 16-bit fields,
+    524,288 tiles) on a sampled loss: dL/dC is non-zero only on the sampled pixels (random ones,
+    the seam and pole tiles, the tiles of the first Gaussians' centres), so the oracle's adjoint
+    of those pixels is the whole gradient."""
+    import torch
+    from paper_2410_20686_gb300.rasterizer import Rasterizer
+    sc = S.random_scene(5000, 16384, 8192, seed=23, sh_degree=1, radius=(0.5, 3.0), log_scale=(-3.0, 0.5))
+    rs = _rs(sh_degree=1)
+    v = sc.views[0]
+    p = O.Params.of(sc)
+    st = oracle_settings(rs)
+    pj = O.project(p, v, st)
+    vis = pj[:, O.PJ_VALID] > 0
+    centres = [(int(u) // 16, int(w) // 16) for u, w in pj[vis][:12, [O.PJ_U, O.PJ_V]]]
+    pix = S.sample_pixels(v.width, v.height, 4096, S.stress_tiles(v.width, v.height) + centres, seed=25)
+    _, _, nc, margins = O.render(p, v, st, pix=pix)
+    amb = O.ambiguous(margins, EPS_SKIP, EPS_TERM, EPS_CLAMP)
+    rng = np.random.default_rng(25)
+    gp = rng.normal(size=(len(pix), 3)) * (~amb)[:, None]
+    ref = O.backward(p, v, st, gp, pix=pix)
+    rast = Rasterizer()
+    m, s, q, o, sh = to_torch(sc)
+    rast.forward(m, s, q, o, sh, sc.views, rs, want_T=False)
+    g = torch.zeros(3, v.height * v.width, device="cuda")
+    g[:, torch.from_numpy(pix.astype(np.int64)).cuda()] = torch.tensor(gp.T, dtype=torch.float32, device="cuda")
+    out = rast.backward([g.view(3, v.height, v.width)])
+    torch.cuda.synchronize()
+    assert rast.status() == 0
+    gpu = {k: t.cpu().numpy().astype(np.float64) for k, t in out.items()}
+    assert (nc > 0).sum() > 1000
+    assert (np.abs(ref["opacity"]) > 0).sum() > 50  # many Gaussians receive a gradient
+    _assert_close(gpu, ref)
