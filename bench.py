@@ -87,26 +87,32 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-                power.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[4:8]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": max(power) if power else None}
+        return summarise_clocks(self.lines)
+
+
+def summarise_clocks(lines):
+    """Median and lowest SM clock, the maximum, the throttle reasons seen active and the peak
+    power of ``nvidia-smi --format=csv,noheader,nounits`` lines of ``ClockSampler.FIELDS``."""
+    sm, smax, reasons, power = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            sm.append(float(parts[0]))
+            smax.append(float(parts[1]))
+            power.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, parts[4:8]):
+            if val.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2], "sm_min_mhz": sm[0], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
 def _gpu_id(torch, dev):
@@ -634,9 +640,12 @@ def run_ours(args):
     K = args.steps
     # per-stage times: an eager run of the step with CUDA events between the stages
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    stage_sampler = ClockSampler(_gpu_id(torch, local))
+    stage_sampler.start()
     for i in range(K):
         step(evs[i])
     torch.cuda.synchronize()
+    stage_clocks = stage_sampler.stop()
     stats = rast.stats()
     assert stats["status"] == 0, stats
     names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
@@ -762,7 +771,7 @@ def run_ours(args):
                       "parallelism": f"replicas x{world}"},
            "roofline": roofline, "kernels_ms": kern, "kernels": kernels, "gpu_launches": graph_launches * K,
            "eager_ms_per_step": eager_ms,
-           "clocks": clocks}
+           "clocks": clocks, "stage_clocks": stage_clocks}
     if e2e:
         out["e2e"] = e2e
     if not args.no_batched:

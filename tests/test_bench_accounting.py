@@ -43,3 +43,16 @@ def test_profiled_traffic_is_tied_to_the_kernel_sources():
     assert t is None or t == bench.PROFILED_TRAFFIC["bytes"]
     other = dict(bench.PROFILED_TRAFFIC, sources=("render_fwd.cu",))
     assert bench.kernel_sources_digest(other) != d
+
+
+def test_clock_summary_reports_median_lowest_and_reasons():
+    # nvidia-smi csv,noheader,nounits lines: sm, max sm, power, active mask, then the four reason flags
+    lines = ["2002, 2070, 250.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "2070, 2070, 420.5, 0x4, Not Active, Not Active, Not Active, Active",
+             "2070, 2070, 400.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "[N/A], 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # skipped
+             "garbage"]
+    c = bench.summarise_clocks(lines)
+    assert (c["sm_mhz"], c["sm_min_mhz"], c["sm_max_mhz"], c["samples"]) == (2070.0, 2002.0, 2070.0, 3)
+    assert c["reasons"] == ["sw_power_cap"] and c["power_w_max"] == 420.5
+    assert bench.summarise_clocks([])["sm_mhz"] is None
