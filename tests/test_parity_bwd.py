@@ -170,3 +170,50 @@ def test_gradients_largest_view_16384x8192():
     assert (nc > 0).sum() > 1000
     assert (np.abs(ref["opacity"]) > 0).sum() > 50  # many Gaussians receive a gradient
     _assert_close(gpu, ref)
+
+
+def _degenerate_scene():
+    sc = S.random_scene(300, 128, 64, seed=61, sh_degree=1, log_scale=(-2.5, 0.5))
+    m, s, o = sc.means, sc.scales, sc.opacity
+    m[0] = [0.0, 2.0, 0.0]  # on the pole axis (rho = 0): culled
+    m[1] = [0.0, -1.5, 0.0]  # on the other pole axis: culled
+    m[2] = [0.0, 0.0, 0.0]  # at the camera centre: culled
+    m[3] = [0.05, 0.05, 0.05]  # inside the near sphere: culled
+    m[4] = [0.5, 0.1, 1.5]
+    o[4] = 0.0  # zero opacity: culled
+    m[5] = [1.0, 0.2, 2.0]
+    s[5] = 0.0  # all scales zero: the splat is the dilation alone
+    o[5] = 0.8
+    m[6] = [-1.0, 0.1, 1.5]
+    s[6] = [0.3, 0.3, 0.0]  # flat disc
+    o[6] = 0.7
+    m[7] = [0.006, -2.0, 0.0]  # rho / r = 3e-3: kept, stretched over the top rows
+    s[7] = 0.05
+    o[7] = 0.9
+    return sc
+
+
+def test_degenerate_gaussians_forward_and_gradients():
+    """Gaussians on the pole axes, at the camera centre, inside the near sphere and with zero
+    opacity are culled on both sides (image unchanged, gradients exactly zero); a Gaussian with
+    all scales zero renders as its screen-space dilation and gets exactly zero scale and rotation
+    gradients; a flat disc and a near-pole Gaussian follow the oracle."""
+    from tests.helpers import compare_image, gpu_render
+    sc = _degenerate_scene()
+    rs = _rs(sh_degree=1)
+    v = sc.views[0]
+    p = O.Params.of(sc)
+    st = oracle_settings(rs)
+    pj = O.project(p, v, st)
+    assert list(pj[:8, O.PJ_VALID]) == [0, 0, 0, 0, 0, 1, 1, 1]
+    imgs, _, _ = gpu_render(sc, rs)
+    ref, _, nc, margins = O.render(p, v, st)
+    compare_image(imgs[0], ref, margins)
+    assert (nc > 0).mean() > 0.3
+    w = _weights(sc, rs, 3)
+    gpu = _gpu_grads(sc, rs, w)
+    _assert_close(gpu, _oracle_grads(sc, rs, w))
+    for k in NAMES:
+        assert np.all(gpu[k][:5] == 0.0), k
+    assert np.all(gpu["scales"][5] == 0.0) and np.all(gpu["quats"][5] == 0.0)
+    assert np.abs(gpu["means"][5]).max() > 0 and np.abs(gpu["means"][7]).max() > 0
