@@ -151,16 +151,18 @@ static double factorial(int k)
     return f;
 }
 
-/* Real orthonormal SH Y_k (k = l^2 + l + m) at the direction with polar angle vt (from +z)
- * and azimuth vp (atan2(y, x)), plus dY/dvt and dY/dvp:
+/* Real orthonormal SH Y_k (k = l^2 + l + m) at the direction with polar angle vt (from +z),
+ * given by its cosine ct and sine st (taken from the direction itself, so that they stay exact
+ * near the poles, where vt from atan2 would round to 0 or to the double nearest pi), and
+ * azimuth vp (atan2(y, x)), plus dY/dvt and dY/dvp:
  *   Y_lm = sqrt(2) K_lm P_l^m cos(m vp)      (m > 0)
  *   Y_l0 = K_l0 P_l^0
  *   Y_lm = sqrt(2) K_l|m| P_l^|m| sin(|m| vp) (m < 0)
  * with K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!). */
-static void sh_basis(int deg, double vt, double vp, double *Y, double *dYt, double *dYp)
+static void sh_basis(int deg, double ct, double st, double vp, double *Y, double *dYt, double *dYp)
 {
     double P[10], dP[10];
-    legendre(cos(vt), sin(vt), P, dP);
+    legendre(ct, st, P, dP);
     for (int l = 0; l <= deg; ++l) {
         for (int m = -l; m <= l; ++m) {
             int am = m < 0 ? -m : m;
@@ -188,9 +190,9 @@ static void sh_basis(int deg, double vt, double vp, double *Y, double *dYt, doub
 void orc_sh_eval(int deg, const double *dir, double *Y)
 {
     double dYt[16], dYp[16];
-    double vt = atan2(sqrt(dir[0] * dir[0] + dir[1] * dir[1]), dir[2]);
+    double n = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
     double vp = atan2(dir[1], dir[0]);
-    sh_basis(deg, vt, vp, Y, dYt, dYp);
+    sh_basis(deg, dir[2] / n, sqrt(dir[0] * dir[0] + dir[1] * dir[1]) / n, vp, Y, dYt, dYp);
 }
 
 /* ---------------------------------------------------------------- depth key */
@@ -339,9 +341,8 @@ have_jacobian:
     double dn = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
     for (int j = 0; j < 3; ++j) pj[PJ_DIR + j] = dv[j] / dn;
     double Y[16], dYt[16], dYp[16];
-    double vt = atan2(sqrt(dv[0] * dv[0] + dv[1] * dv[1]), dv[2]);
     double vp = atan2(dv[1], dv[0]);
-    sh_basis(s->sh_degree, vt, vp, Y, dYt, dYp);
+    sh_basis(s->sh_degree, dv[2] / dn, sqrt(dv[0] * dv[0] + dv[1] * dv[1]) / dn, vp, Y, dYt, dYp);
     int K = (s->sh_degree + 1) * (s->sh_degree + 1);
     for (int c = 0; c < 3; ++c) {
         double acc = 0.5;
@@ -646,9 +647,9 @@ have_dt:
     double dv[3] = {mean[0] - cam[0], mean[1] - cam[1], mean[2] - cam[2]};
     double sxy2 = dv[0] * dv[0] + dv[1] * dv[1], sxy = sqrt(sxy2);
     double n2 = sxy2 + dv[2] * dv[2];
-    double vt = atan2(sxy, dv[2]), vp = atan2(dv[1], dv[0]);
+    double nn = sqrt(n2), vp = atan2(dv[1], dv[0]);
     double Y[16], dYt[16], dYp[16];
-    sh_basis(s->sh_degree, vt, vp, Y, dYt, dYp);
+    sh_basis(s->sh_degree, dv[2] / nn, sxy / nn, vp, Y, dYt, dYp);
     int K = (s->sh_degree + 1) * (s->sh_degree + 1);
     double dLdvt = 0.0, dLdvp = 0.0;
     for (int c = 0; c < 3; ++c) {
@@ -660,10 +661,27 @@ have_dt:
             dLdvp += gc * sh[3 * k + c] * dYp[k];
         }
     }
-    /* vt = atan2(sqrt(x^2 + y^2), z), vp = atan2(y, x) of the unnormalised direction */
-    double dvtdv[3] = {dv[0] * dv[2] / (n2 * sxy), dv[1] * dv[2] / (n2 * sxy), -sxy / n2};
-    double dvpdv[3] = {-dv[1] / sxy2, dv[0] / sxy2, 0.0};
-    for (int j = 0; j < 3; ++j) gm[j] += dLdvt * dvtdv[j] + dLdvp * dvpdv[j];
+    if (sxy > 1e-100 * nn) {
+        /* vt = atan2(sqrt(x^2 + y^2), z), vp = atan2(y, x) of the unnormalised direction */
+        double dvtdv[3] = {dv[0] * dv[2] / (n2 * sxy), dv[1] * dv[2] / (n2 * sxy), -sxy / n2};
+        double dvpdv[3] = {-dv[1] / sxy2, dv[0] / sxy2, 0.0};
+        for (int j = 0; j < 3; ++j) gm[j] += dLdvt * dvtdv[j] + dLdvp * dvpdv[j];
+    } else {
+        /* direction on the z axis (to 1e-100), where the (vt, vp) chart is singular. The colour
+         * is smooth on the sphere, so its gradient there is the limit along +x (vp = 0) and
+         * along +y (vp = pi/2); at either pole d vt / dx = d vt / dy = 1 / z, and moving along z
+         * leaves the direction unchanged. */
+        double Yq[16], dYtq[16], dYpq[16];
+        for (int a = 0; a < 2; ++a) {
+            sh_basis(s->sh_degree, dv[2] > 0.0 ? 1.0 : -1.0, 0.0, a == 0 ? 0.0 : 0.5 * ORC_PI, Yq, dYtq, dYpq);
+            double D = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                if (pj[PJ_CLAMP + c] != 0.0) continue;
+                for (int k = 0; k < K; ++k) D += g2[G2_R + c] * sh[3 * k + c] * dYtq[k];
+            }
+            gm[a] += D / dv[2];
+        }
+    }
 
     /* Sigma = M M^T, M = R diag(s)  ->  dL/dM = (dSig + dSig^T) M */
     double qn = sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);

@@ -175,3 +175,21 @@ def test_raw_parameter_mode_agrees_with_activated_mode():
     y = D.apply(mu, np.log(scales), q, opac, sh, act, noise, raw_params=True)
     np.testing.assert_allclose(x[0], y[0], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(x[1], np.exp(y[1]), rtol=1e-12)
+
+
+def test_paper_hyperparameters_are_the_defaults():
+    """The densification constants of App. A.1 (stored as text with their citation) are the
+    oracle's constants and the defaults of the GPU path's parameter block."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "app_a1_densify.txt")
+    vals = {}
+    for ln in open(path):
+        ln = ln.split("#", 1)[0].split()
+        if ln:
+            vals[ln[0]] = float(ln[1])
+    assert (D.TAU_MIN, D.TAU_MAX, D.PERCENT_DENSE) == (
+        vals["densify_grad_threshold_min"], vals["densify_grad_threshold_max"], vals["percent_dense"])
+    from paper_2410_20686_gb300.densify import DensifyParams
+    p = DensifyParams()
+    assert (p.tau_min, p.tau_max, p.percent_dense) == (D.TAU_MIN, D.TAU_MAX, D.PERCENT_DENSE)
+    assert vals["densify_until_iter"] < vals["iterations"]

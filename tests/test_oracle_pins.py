@@ -428,6 +428,33 @@ def test_p9_adjoint_matches_central_differences(seed):
     assert checked > 40
 
 
+@pytest.mark.parametrize("z", [2.0, -1.5])
+def test_p9_adjoint_on_the_sh_axis_matches_central_differences(z):
+    """A mean straight above or below the camera centre along world z, the axis on which the
+    SH basis's angle chart (polar angle from +z, azimuth atan2(y, x)) is singular: the colour
+    is smooth there, and the adjoint's mean gradient must equal central differences."""
+    deg = 3
+    W, H = 40, 20
+    sc = S.random_scene(6, W, H, seed=131, sh_degree=deg, radius=(1.0, 3.0), log_scale=(-1.8, 0.3))
+    p = O.Params.of(sc)
+    from scipy.spatial.transform import Rotation
+    R = Rotation.from_euler("xyz", [0.3, 0.2, -0.4]).as_matrix()
+    cam = np.array([0.1, -0.2, 0.3])
+    view = _view(W, H, R, -R @ cam)  # camera centre at cam
+    p.means[0] = cam + np.array([0.0, 0.0, z])
+    p.scales[0] = [0.2, 0.15, 0.25]
+    p.opacity[0] = 0.9
+    st = O.Settings(sh_degree=deg, bg=(0.3, 0.1, 0.2))
+    assert O.project(p, view, st)[0, O.PJ_VALID] == 1
+    wts = np.random.default_rng(7).normal(size=(3, H, W))
+    g = O.backward(p, view, st, wts)
+    assert np.all(np.isfinite(g["means"]))
+    for j in range(3):
+        fd = O.fd_grad(p, view, st, wts, "means", j, 1e-6)
+        ad = g["means"][0, j]
+        assert abs(ad - fd) <= 2e-6 * max(abs(fd), 1e-3 * np.abs(g["means"]).max()) + 1e-9, (j, ad, fd)
+
+
 def test_screen_space_gradients_match_finite_differences_of_the_blend():
     """dL/d(u, v, conic, opacity, rgb) of the reverse blend, checked by perturbing a single
     Gaussian's screen-space quantities through its 3D parameters is covered above; here the
