@@ -217,3 +217,28 @@ def test_degenerate_gaussians_forward_and_gradients():
         assert np.all(gpu[k][:5] == 0.0), k
     assert np.all(gpu["scales"][5] == 0.0) and np.all(gpu["quats"][5] == 0.0)
     assert np.abs(gpu["means"][5]).max() > 0 and np.abs(gpu["means"][7]).max() > 0
+
+
+def test_gaussians_exactly_on_the_seam():
+    """Means straight behind the camera (azimuth exactly +-180 deg, u = W on the wrapped image),
+    one with a negative-zero x, one a hair past the seam, and one straight ahead: images and all
+    five gradients against the oracle."""
+    from tests.helpers import compare_image, gpu_render
+    sc = S.random_scene(200, 128, 64, seed=71, sh_degree=1, log_scale=(-2.5, 0.5))
+    m, s, o = sc.means, sc.scales, sc.opacity
+    m[0] = [0.0, 0.0, -2.0]
+    m[1] = [-0.0, 0.3, -1.5]
+    m[2] = [0.0, 0.0, 2.0]
+    m[3] = [1e-7, -0.2, -3.0]
+    s[0:4] = np.array([0.15, 0.1, 0.1, 0.2], np.float32)[:, None]
+    o[0:4] = [0.9, 0.8, 0.9, 0.7]
+    rs = _rs(sh_degree=1)
+    v = sc.views[0]
+    p = O.Params.of(sc)
+    st = oracle_settings(rs)
+    imgs, _, _ = gpu_render(sc, rs)
+    ref, _, nc, margins = O.render(p, v, st)
+    compare_image(imgs[0], ref, margins)
+    assert (nc[:, 0] > 0).sum() > 10 and (nc[:, -1] > 0).sum() > 10  # both image edges covered
+    w = _weights(sc, rs, 4)
+    _assert_close(_gpu_grads(sc, rs, w), _oracle_grads(sc, rs, w))
