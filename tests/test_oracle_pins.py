@@ -455,6 +455,48 @@ def test_p9_adjoint_on_the_sh_axis_matches_central_differences(z):
         assert abs(ad - fd) <= 2e-6 * max(abs(fd), 1e-3 * np.abs(g["means"]).max()) + 1e-9, (j, ad, fd)
 
 
+@pytest.mark.parametrize("mean,scale,R", [
+    ([0.0, 0.0, -2.0], 0.2, None),        # straight behind: azimuth exactly 180 deg, on the seam
+    ([1e-9, 0.3, -2.0], 0.2, None),       # a hair to one side of the seam
+    ([-1e-9, 0.3, -2.0], 0.2, None),      # and to the other
+    ([0.0, -2.0, 4e-4], 0.05, None),      # 0.011 deg from the upper pole (rho / r = 2e-4)
+    ([0.0, 2.0, 1e-3], 0.05, None),       # 0.029 deg from the lower pole
+    ([0.12, 0.1, 0.15], 0.02, None),      # just outside the near sphere (r = 0.22)
+    ([0.0, 0.0, 2.0], 0.2, [[0, 0, 1], [0, 1, 0], [-1, 0, 0]]),  # rotated view, on the SH basis's axis
+])
+def test_p9_adjoint_at_special_points(mean, scale, R):
+    """One anisotropic Gaussian at a point where the projection or the SH basis is special: the
+    adjoint of every parameter element against central differences."""
+    rng = np.random.default_rng(3)
+    W, H = 64, 32
+    quat = rng.normal(size=(1, 4))
+    p = O.Params(np.array([mean], float), np.array([[scale, 0.6 * scale, 0.3 * scale]]), quat / np.linalg.norm(quat),
+                 np.array([0.8]), rng.normal(scale=0.3, size=(1, 16, 3)))
+    view = _view(W, H, R)
+    st = O.Settings(sh_degree=3, bg=(0.2, 0.1, 0.3))
+    assert O.project(p, view, st)[0, O.PJ_VALID] == 1
+    wts = rng.normal(size=(3, H, W))
+    g = O.backward(p, view, st, wts)
+    _, _, nc0, _ = O.render(p, view, st)
+    checked = 0
+    for name, arr in p.arrays().items():
+        for idx in range(arr.size):
+            x0 = arr.flat[idx]
+            h = 1e-6 * max(1.0, abs(x0))
+            arr.flat[idx] = x0 + h
+            _, _, ncp, _ = O.render(p, view, st)
+            arr.flat[idx] = x0 - h
+            _, _, ncm, _ = O.render(p, view, st)
+            arr.flat[idx] = x0
+            if not (np.array_equal(ncp, nc0) and np.array_equal(ncm, nc0)):
+                continue
+            fd = O.fd_grad(p, view, st, wts, name, idx, h)
+            scale_ = max(abs(fd), 1e-3 * np.abs(g[name]).max(), 1e-9)
+            assert abs(g[name].flat[idx] - fd) <= 1e-5 * scale_, (name, idx, g[name].flat[idx], fd)
+            checked += 1
+    assert checked >= 50
+
+
 def test_screen_space_gradients_match_finite_differences_of_the_blend():
     """dL/d(u, v, conic, opacity, rgb) of the reverse blend, checked by perturbing a single
     Gaussian's screen-space quantities through its 3D parameters is covered above; here the
