@@ -242,3 +242,29 @@ def test_gaussians_exactly_on_the_seam():
     assert (nc[:, 0] > 0).sum() > 10 and (nc[:, -1] > 0).sum() > 10  # both image edges covered
     w = _weights(sc, rs, 4)
     _assert_close(_gpu_grads(sc, rs, w), _oracle_grads(sc, rs, w))
+
+
+def test_gaussians_within_a_twentieth_of_a_degree_of_the_poles():
+    """Means 0.006-0.05 deg from either pole (rho / r from 1.2e-4, just above the 1e-4 cull, to
+    8.7e-4), where J_omni's 1 / rho terms are largest and each footprint stretches over whole
+    rows: images and all five gradients against the oracle."""
+    from tests.helpers import compare_image, gpu_render
+    rng = np.random.default_rng(9)
+    n, W, H = 80, 128, 64
+    sc = S.random_scene(n, W, H, seed=91, sh_degree=1, log_scale=(-2.5, 0.4))
+    r = rng.uniform(1.0, 3.0, n)
+    eps = np.radians(rng.uniform(0.006, 0.05, n))
+    phi = rng.uniform(-np.pi, np.pi, n)
+    theta = np.where(rng.uniform(size=n) < 0.5, 1.0, -1.0) * (np.pi / 2 - eps)
+    sc.means[:] = np.stack([r * np.cos(theta) * np.sin(phi), -r * np.sin(theta), r * np.cos(theta) * np.cos(phi)],
+                           1).astype(np.float32)
+    rs = _rs(sh_degree=1)
+    p = O.Params.of(sc)
+    st = oracle_settings(rs)
+    assert O.project(p, sc.views[0], st)[:, O.PJ_VALID].sum() == n
+    imgs, _, _ = gpu_render(sc, rs)
+    ref, _, nc, margins = O.render(p, sc.views[0], st)
+    compare_image(imgs[0], ref, margins)
+    assert (nc[0] > 0).all() and (nc[-1] > 0).all()
+    w = _weights(sc, rs, 5)
+    _assert_close(_gpu_grads(sc, rs, w), _oracle_grads(sc, rs, w))
