@@ -170,7 +170,8 @@ RECORD_BYTES = 52
 ACC_BYTES = 36
 
 
-def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_tflops, alu_measured):
+def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_tflops, alu_measured,
+                    ex2_measured=None):
     items, vis, pairs = n, stats["visible"], stats["pairs_sorted"]
     hbm = {
         "preprocess": n * param_bytes(sh_degree) + vis * RECORD_BYTES,
@@ -192,6 +193,12 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
                   "frac": tf / alu_tflops}
         if alu_measured:
             out[k]["frac_of_measured_ffma"] = tf / alu_measured
+        # SFU: one ex2 per blended entry (Eq. 2's exponential; the backward recomputes the forward's)
+        ex2 = stats["blended"] / (kern[k] * 1e-3) / 1e9
+        out[k]["ex2"] = stats["blended"]
+        out[k]["ex2_gops"] = ex2
+        if ex2_measured:
+            out[k]["frac_of_measured_ex2"] = ex2 / ex2_measured
     return out
 
 
@@ -235,8 +242,9 @@ def profiled_traffic():
 # ------------------------------------------------------------------ CPU oracle leg
 
 def oracle_sample(scene, n_pix, seed=0):
-    """Oracle forward + adjoint on n_pix seeded pixels; returns timings and the extrapolated
-    full-frame iteration time."""
+    """Oracle forward and adjoint on n_pix seeded pixels, timed separately; returns the timings and
+    the extrapolated full-frame times of each pass (per-Gaussian work once, per-pixel work times
+    the frame's pixels)."""
     import numpy as np
     from oracle import oracle as O
     from paper_2410_20686_gb300 import scenes as S
@@ -256,18 +264,22 @@ def oracle_sample(scene, n_pix, seed=0):
     t3 = time.perf_counter()
     O.backward(p, v, st, g, pix=pix)
     t4 = time.perf_counter()
-    fixed = (t1 - t0) + (t3 - t2)              # per-Gaussian projection, sort, adjoint chain
-    per_pix = ((t2 - t1) + (t4 - t3)) / max(len(pix) - 1, 1)
-    full = fixed + per_pix * v.width * v.height
-    return {"sample_s": t4 - t0, "full_iter_s": full, "pixels": len(pix), "threads": O.num_threads()}
+    px = v.width * v.height
+    span = max(len(pix) - 1, 1)
+    # the one-pixel call is the per-Gaussian cost (projection, sort; the adjoint's chain rule)
+    fwd = (t1 - t0) + (t2 - t1) / span * px
+    adj = (t3 - t2) + (t4 - t3) / span * px
+    return {"sample_s": t4 - t0, "full_iter_s": fwd + adj, "forward_s": fwd, "adjoint_s": adj,
+            "pixels": len(pix), "threads": O.num_threads()}
 
 
 def cpu_baseline(scene):
     r = oracle_sample(scene, CPU_SAMPLE_PIXELS)
     return {"value": 1.0 / r["full_iter_s"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
-            "sample": f"{r['pixels']} seeded pixels of the 2048x1024 view, forward + adjoint, per-pixel time "
-                      f"extrapolated to all pixels plus the full per-Gaussian projection / adjoint "
-                      f"({r['sample_s']:.1f} s of CPU work)"}
+            "forward_s_per_frame": r["forward_s"], "adjoint_s_per_frame": r["adjoint_s"],
+            "sample": f"{r['pixels']} seeded pixels of the 2048x1024 view, forward and adjoint timed separately, "
+                      f"per-pixel time extrapolated to all pixels plus the full per-Gaussian projection / adjoint "
+                      f"({r['sample_s']:.1f} s of CPU work); extrapolated"}
 
 
 def run_reference(args):
@@ -280,11 +292,13 @@ def run_reference(args):
     scene = S.config2(n=args.n, width=args.width)
     for w in range(args.warmup):
         oracle_sample(scene, 64, seed=100 + w)
-    times = []
+    times, fwd, adj = [], [], []
     res = None
     for k in range(args.steps):
         res = oracle_sample(scene, 256, seed=k)
         times.append(res["full_iter_s"])
+        fwd.append(res["forward_s"])
+        adj.append(res["adjoint_s"])
     import statistics
     full = statistics.median(times)
     value = 1.0 / full
@@ -293,7 +307,10 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
-                            "sample": "each step: 256 seeded pixels, forward + adjoint, extrapolated to the full frame"},
+                            "forward_s_per_frame": statistics.median(fwd),
+                            "adjoint_s_per_frame": statistics.median(adj),
+                            "sample": "each step: 256 seeded pixels, forward and adjoint timed separately, "
+                                      "extrapolated to the full frame"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -535,6 +552,104 @@ def run_cubemap(torch, dev, params, target_erp, rs, steps=20, warmup=3):
             "ms_per_frame": ms, "iter_per_s": 1e3 / ms, "pixels": 6 * face * face}
 
 
+# ------------------------------------------------------------------ end to end through the C ABI
+
+GRAD_NAMES = ("means", "scales", "quats", "opacity", "sh")
+
+
+def run_e2e_abi(torch, dev, rs, view, host_in, steps, warmup, barrier):
+    """fwd+bwd iterations/s through the library's C ABI with host buffers: every step copies the
+    five parameter arrays and the target from pinned host memory to the device, calls
+    odgs_preprocess -> odgs_bin_sort -> odgs_render_fwd -> fused L1 loss -> odgs_render_bwd ->
+    odgs_preprocess_bwd (eager calls, no graph), and copies all five gradient arrays and the loss
+    back to pinned host memory, where the host reads them. Uploads of step i+1 (one copy stream) and
+    downloads of step i (another) overlap step i+1's kernels through two device input and gradient
+    sets."""
+    from paper_2410_20686_gb300.loss import l1_dssim
+    from paper_2410_20686_gb300.rasterizer import Rasterizer
+    sets = [[torch.empty(h.shape, dtype=h.dtype, device=dev) for h in host_in] for _ in range(2)]
+    gsets = [{k: torch.empty_like(t) for k, t in zip(GRAD_NAMES, st[:5])} for st in sets]
+    host_g = [{k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in g.items()} for g in gsets]
+    loss_host = [torch.empty((), dtype=torch.float32).pin_memory() for _ in range(2)]
+    image = torch.empty((3, view.height, view.width), dtype=torch.float32, device=dev)
+    rast = Rasterizer(dev, capacity_mode="query", headroom=1.1)
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    main = torch.cuda.current_stream(dev)
+    loaded, freed, computed, downloaded = ([torch.cuda.Event() for _ in range(2)] for _ in range(4))
+
+    def upload(j):
+        with torch.cuda.stream(up):
+            up.wait_event(freed[j])  # the step that last read input set j has finished
+            for h, d in zip(host_in, sets[j]):
+                d.copy_(h, non_blocking=True)
+            loaded[j].record(up)
+
+    def compute(j):
+        main.wait_event(loaded[j])
+        main.wait_event(downloaded[j])  # gradient set j has been copied out
+        p = sets[j]
+        rast.preprocess(*p[:5], [view], rs)
+        rast.bin_sort()
+        rast.render_fwd([image], want_T=False)
+        loss, gl = l1_dssim([image], [p[5]], lam=0.0, area_weight=False)
+        rast.render_bwd([gl[0]])
+        rast.preprocess_bwd(gsets[j])
+        freed[j].record(main)
+        computed[j].record(main)
+        loss.record_stream(down)
+        with torch.cuda.stream(down):
+            down.wait_event(computed[j])
+            for k in GRAD_NAMES:
+                host_g[j][k].copy_(gsets[j][k], non_blocking=True)
+            loss_host[j].copy_(loss.reshape(()), non_blocking=True)
+            downloaded[j].record(down)
+
+    def consume(j, out):
+        downloaded[j].synchronize()
+        out.append((float(loss_host[j]), float(host_g[j]["opacity"][0])))
+
+    def run(n):
+        results = []
+        for j in range(2):
+            freed[j].record(main)
+            downloaded[j].record(main)
+        upload(0)
+        for i in range(n):
+            j = i % 2
+            if i + 1 < n:
+                upload(1 - j)
+            compute(j)
+            if i > 0:  # the previous step's gradients and loss, read while this step runs
+                consume(1 - j, results)
+        consume((n - 1) % 2, results)
+        return results
+
+    # size the pair buffer once (one host read of the pair count), then no host synchronisation
+    upload(0)
+    main.wait_event(loaded[0])
+    rast.forward(*sets[0][:5], [view], rs, want_T=False)
+    torch.cuda.synchronize(dev)
+    rast.capacity_mode = "fixed"
+    run(warmup)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    res = run(steps)
+    torch.cuda.synchronize(dev)
+    seconds = time.perf_counter() - t0
+    barrier()
+    import math
+    assert len(res) == steps and all(math.isfinite(a) and math.isfinite(b) for a, b in res)
+    assert rast.status() == 0
+    h2d = sum(h.numel() * h.element_size() for h in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in gsets[0].values()) + 4
+    return {"seconds": seconds, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "path": "C-ABI calls every step (odgs_preprocess, odgs_bin_sort, odgs_render_fwd, fused L1 loss, "
+                    "odgs_render_bwd, odgs_preprocess_bwd) from pinned host parameters and target; all five "
+                    "gradient arrays and the loss copied back to pinned host memory and read by the host",
+            "overlap": "uploads of step i+1 and downloads of step i on two copy streams beside step i+1's kernels"}
+
+
 # ------------------------------------------------------------------ multi-process plumbing
 
 def dist_env():
@@ -730,9 +845,17 @@ def run_ours(args):
         te = max_over_ranks(time.perf_counter() - t0, world, dev)
         assert len(losses) == K and all(np.isfinite(losses)), losses
         assert all(f.status() == 0 for f in frames)
-        e2e = {"value": job_rate(world, K, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
-               "overlap": "uploads on a second stream into the inputs of two graphed frames; losses read one "
-                          "step behind"}
+        e2e_graph = {"value": job_rate(world, K, te), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": 4,
+                     "overlap": "uploads on a second stream into the inputs of two graphed frames; losses read "
+                                "one step behind; the gradients stay on the device (a training loop's reading)"}
+        del frames[1:]
+        torch.cuda.empty_cache()
+        barrier()
+        abi = run_e2e_abi(torch, dev, rs, view, host, K, max(3, args.warmup), barrier)
+        te = max_over_ranks(abi.pop("seconds"), world, dev)
+        e2e = dict(value=job_rate(world, K, te), unit=UNIT, **abi)
+        e2e["graph_replay"] = e2e_graph
 
     if rank != 0:
         if world > 1:
@@ -744,7 +867,8 @@ def run_ours(args):
     tiles = (view.width // tw) * ((view.height + th - 1) // th)
     pair_passes = (max(1, (tiles - 1).bit_length()) + 7) // 8  # 8-bit passes over the tile id
     kernels = stage_rooflines(kern, stats, args.n, 3, tiles, pair_passes, float(peaks["hbm_gbs"]), peak_tf,
-                              measured["ffma_tflops"] if measured else None)
+                              measured["ffma_tflops"] if measured else None,
+                              measured["ex2_gops"] if measured else None)
     dom = max(("render_fwd", "render_bwd"), key=lambda k: kern[k])
     d = kernels[dom]
     roofline = {"bound": "alu", "kernel": "k_render_fwd" if dom == "render_fwd" else "k_render_bwd",
@@ -758,6 +882,7 @@ def run_ours(args):
     if measured:
         roofline["peak_measured"] = measured
         roofline["frac_of_measured_ffma"] = d.get("frac_of_measured_ffma")
+        roofline["ex2_frac_of_measured"] = d.get("frac_of_measured_ex2")
 
     out = {"metric": METRIC, "value": job_rate(world, K, elapsed), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak",

@@ -198,20 +198,62 @@ odgs_status odgs_frame_stats(odgs_ctx *ctx, odgs_stats *out, void *stream);
 /* Synchronizes the stream and returns the device status bits (ODGS_DEV_*) in *bits. */
 odgs_status odgs_get_status(odgs_ctx *ctx, uint32_t *bits, void *stream);
 
+/* Bound of the device-side waits (test and tuning hook). The sorts of odgs_bin_sort wait for the
+ * per-digit counts of earlier sort tiles (decoupled look-back); a sort CTA that has read those
+ * words `reads` times without reaching a complete prefix gives up, sets ODGS_DEV_TIMEOUT and
+ * finishes with wrong (but in-bounds) positions: the frame's lists, images and gradients are then
+ * invalid but finite, nothing is written or read out of bounds, and odgs_query_pairs returns
+ * ODGS_ERR_TIMEOUT. Default 4194304 reads (seconds of waiting). 0 makes every sort of more than
+ * one tile (more than 2048 keys) give up at once, which exercises the failure path without a GPU
+ * fault. Takes effect from the next odgs_bin_sort of this context. */
+odgs_status odgs_set_wait_limit(odgs_ctx *ctx, uint32_t reads);
+
+/* Copies of the frame's integer binning state, for tests and inspection: the order in which
+ * every tile blends its Gaussians, "sorting by depth" (Sec. 3.1, the order of Eq. 3). Valid after
+ * odgs_bin_sort (or an odgs_render_bwd that rebuilt the lists). Asynchronous device-to-device
+ * copies on `stream` into caller buffers (device, uint32); each pointer may be NULL:
+ *   depth_keys  [n_items]  the depth keys in sorted order: IEEE bits of the FP32 depth (radial
+ *                          distance |t| for ERP views, t_z for pinhole views), 0xFFFFFFFF for an
+ *                          item culled or covering no pixel centre;
+ *   depth_items [n_items]  the item (view * n + Gaussian) of each sorted key (ties by item);
+ *   pair_tiles  [n_pairs]  the global tile id (view's first tile + row * tiles_x + column) of each
+ *                          (tile, item) pair, tile-sorted; within a tile the pairs keep depth order;
+ *   pair_items  [n_pairs]  the item of each pair;
+ *   ranges      [2 * n_tiles]  [start, end) of every tile's run in the pair list ([0, 0) if none).
+ * n_items must be views * n, n_tiles the frame's tile count (sum over views of
+ * (W / tile_w) * ceil(H / tile_h)), n_pairs at most the pair capacity (odgs_frame_stats gives
+ * the pairs sorted); otherwise ODGS_ERR_INVALID_ARG and nothing is copied. */
+odgs_status odgs_debug_lists(odgs_ctx *ctx, uint32_t *depth_keys, uint32_t *depth_items, size_t n_items,
+                             uint32_t *pair_tiles, uint32_t *pair_items, size_t n_pairs, uint32_t *ranges,
+                             size_t n_tiles, void *stream);
+
+/* Copy of the per-(view, Gaussian) screen-space gradients accumulated by the last
+ * odgs_render_bwd, for tests and inspection (the reverse of Eq. 2-3 before the chain rule of
+ * App. A.3). Asynchronous device-to-device copy on `stream` into out: device float32
+ * [n_items][12], n_items = views * n, item = view * n + Gaussian, per item
+ *   dL/du, dL/dv (ERP mean, pixels), dL/da, dL/db, dL/dc (conic, power = ln o - (a dx^2 +
+ *   2 b dx dy + c dy^2) / 2), dL/do (opacity), dL/dr, dL/dg, dL/db (colour), 0, 0, 0.
+ * ODGS_ERR_STATE before odgs_render_bwd; ODGS_ERR_INVALID_ARG if n_items differs. */
+odgs_status odgs_debug_screen_grads(odgs_ctx *ctx, float *out, size_t n_items, void *stream);
+
 /* Forward render of ONE view that allocates nothing and needs no workspace or pair buffer, for
  * callers that cannot call cudaMalloc (a plugin or frame callback inside a host application that
  * owns a fixed device-memory budget, or a real-time loop where cudaMalloc / cudaFree would
  * synchronize the device). The paper has no counterpart: it is a packaging of the forward path
  * (odgs_preprocess + odgs_bin_sort + odgs_render_fwd, same kernels, same image).
- * Inputs: g, view, s (host structs; device arrays as for odgs_preprocess). Outputs: image
- * [3][H][W] and final_T [H][W] (device, final_T may be NULL), and status_out (device, one
- * uint32_t) which receives the device status bits (ODGS_DEV_CAPACITY when the frame had more
- * pairs than fit) without a host synchronization.
+ * Inputs: g, view, s (host structs; device arrays as for odgs_preprocess, checked by the same
+ * rules: a non-finite pose, an invalid setting or a misaligned array returns ODGS_ERR_INVALID_ARG).
+ * The view may be ERP (model 0) or pinhole (model 1). Outputs: image [3][H][W] and final_T
+ * [H][W] (device, final_T may be NULL), and status_out (device, one uint32_t) which receives the
+ * device status bits (ODGS_DEV_CAPACITY when the frame had more pairs than fit: the pairs beyond
+ * the capacity are dropped, the image stays finite) without a host synchronization.
  * Scratch: a 32 MiB file-scope device array that every GPU using this library holds until the
  * process exits. Limits: n <= 32768 Gaussians, W * H <= 524288 pixels, pairs up to what fits in
  * the rest of the array (about 1.4 million); larger sizes return ODGS_ERR_INVALID_ARG and
  * launch nothing. The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream capture. All calls
+ * device, with that device current); make that first call before any stream capture. The address
+ * is kept for the life of the process, so the device must not be reset (cudaDeviceReset) between
+ * calls: after a reset the kept address no longer refers to the array. All calls
  * share the array and each one resets the parts that must start at zero; calls whose work
  * overlaps on the GPU (other streams, unordered host threads) race on it. */
 odgs_status odgs_render_fwd_static(const odgs_gaussians *g, const odgs_view *view, const odgs_settings *s,

@@ -756,6 +756,25 @@ int orc_backward(int n, const double *means, const double *scales, const double 
     return 0;
 }
 
+/* The chain rule alone (App. A.3): parameter gradients from given per-Gaussian screen-space
+ * gradients g2 [n][9] (dL/du, dL/dv, dL/da, dL/db, dL/dc, dL/do, dL/dr, dL/dg, dL/db) of one view,
+ * ACCUMULATED into gm, gs, gq, go, gsh as in orc_backward. It lets a test feed the same
+ * screen-space gradients to two chain-rule implementations. */
+int orc_chain(int n, const double *means, const double *scales, const double *quats, const double *opacity,
+              const double *sh, const orc_view *v, const orc_settings *s, const double *g2, double *gm,
+              double *gs, double *gq, double *go, double *gsh)
+{
+    double *pj = (double *)malloc(sizeof(double) * PJ_NFIELDS * (size_t)(n > 0 ? n : 1));
+    orc_project(n, means, scales, quats, opacity, sh, v, s, pj);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        project_adjoint(means + 3 * i, scales + 3 * i, quats + 4 * i, sh + (size_t)3 * s->sh_coeffs * i, v, s,
+                        pj + (size_t)PJ_NFIELDS * i, g2 + (size_t)G2_N * i, gm + 3 * i, gs + 3 * i, gq + 4 * i,
+                        go + i, gsh + (size_t)3 * s->sh_coeffs * i);
+    free(pj);
+    return 0;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

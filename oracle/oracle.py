@@ -60,6 +60,7 @@ def lib():
         L.orc_render.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, C.c_int, ip, dp, dp, ip, dp]
         L.orc_backward.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, C.c_int, ip, dp,
                                    dp, dp, dp, dp, dp, dp]
+        L.orc_chain.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, dp, dp, dp, dp, dp, dp]
         L.orc_sh_eval.argtypes = [C.c_int, dp, dp]
         L.orc_depth_f32.argtypes = [dp, vp]
         L.orc_depth_f32.restype = C.c_float
@@ -180,6 +181,19 @@ def backward(p: Params, view, st: Settings, dLdC, pix=None, want_g2=False):
                    _ptr(g["quats"]), _ptr(g["opacity"]), _ptr(g["sh"]), _ptr(g2))
     if want_g2:
         g["screen"] = g2[: p.n]
+    return g
+
+
+def chain(p: Params, view, st: Settings, g2):
+    """The chain rule alone (App. A.3): FP64 parameter gradients of one view from given
+    per-Gaussian screen-space gradients g2 [n, 9] (order of G2_NAMES)."""
+    L = lib()
+    g2 = np.ascontiguousarray(g2, dtype=np.float64).reshape(p.n, 9)
+    g = dict(means=np.zeros_like(p.means), scales=np.zeros_like(p.scales),
+             quats=np.zeros_like(p.quats), opacity=np.zeros_like(p.opacity), sh=np.zeros_like(p.sh))
+    L.orc_chain(p.n, _ptr(p.means), _ptr(p.scales), _ptr(p.quats), _ptr(p.opacity), _ptr(p.sh),
+                C.byref(_cview(view)), C.byref(_csettings(st, p.sh)), _ptr(g2), _ptr(g["means"]),
+                _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opacity"]), _ptr(g["sh"]))
     return g
 
 

@@ -26,7 +26,8 @@ EXPORTED = ("odgs_create", "odgs_destroy", "odgs_workspace_size", "odgs_pair_buf
             "odgs_render_bwd", "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status",
             "odgs_render_fwd_static", "odgs_measure_peaks", "odgs_last_launch_count", "odgs_status_string",
             "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply", "odgs_adam_step",
-            "odgs_loss_scratch_size", "odgs_loss_l1_dssim")
+            "odgs_loss_scratch_size", "odgs_loss_l1_dssim", "odgs_set_wait_limit", "odgs_debug_lists",
+            "odgs_debug_screen_grads")
 
 
 class OdgsError(RuntimeError):
@@ -130,6 +131,9 @@ def load(path: str = LIB_PATH):
     L.odgs_loss_l1_dssim.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(LossParams), vp, vp, vp, sz, vp]
     L.odgs_densify_apply.argtypes = [C.POINTER(Gaussians), C.c_int, C.c_int, vp, vp, C.POINTER(ParamsOut), C.c_int,
                                      vp, vp, sz, vp]
+    L.odgs_set_wait_limit.argtypes = [vp, C.c_uint32]
+    L.odgs_debug_lists.argtypes = [vp, vp, vp, sz, vp, vp, sz, vp, sz, vp]
+    L.odgs_debug_screen_grads.argtypes = [vp, vp, sz, vp]
     L.odgs_last_launch_count.argtypes = [vp]
     L.odgs_last_launch_count.restype = C.c_int
     L.odgs_status_string.argtypes = [C.c_int]
@@ -138,7 +142,8 @@ def load(path: str = LIB_PATH):
                  "odgs_query_pairs", "odgs_bin_sort", "odgs_render_fwd", "odgs_render_bwd",
                  "odgs_preprocess_bwd", "odgs_frame_stats", "odgs_get_status", "odgs_render_fwd_static",
                  "odgs_measure_peaks", "odgs_densify_select", "odgs_densify_scratch_size", "odgs_densify_apply",
-                 "odgs_adam_step", "odgs_loss_scratch_size", "odgs_loss_l1_dssim"):
+                 "odgs_adam_step", "odgs_loss_scratch_size", "odgs_loss_l1_dssim", "odgs_set_wait_limit",
+                 "odgs_debug_lists", "odgs_debug_screen_grads"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -25,10 +25,6 @@ struct PairLayout {
     size_t keys0, keys1, vals0, vals1, hist, ctr, lb, total;
 };
 
-struct Geometry {
-    int total_tiles = 0, total_pixels = 0, total_trig = 0, key_bits = 1;
-    size_t n_items = 0;
-};
 
 Layout make_layout(size_t items, const Geometry& g) {
     Layout L{};
@@ -82,9 +78,9 @@ PairLayout make_pair_layout(size_t cap) {
     return P;
 }
 
-bool finite(float x) { return std::isfinite(x); }
+}  // namespace
 
-odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
+odgs_status odgs::check_settings(const odgs_settings* s, odgs_settings* out) {
     if (!s) return ODGS_ERR_INVALID_ARG;
     odgs_settings t = *s;
     if (t.sh_degree < 0 || t.sh_degree > 3) return ODGS_ERR_INVALID_ARG;
@@ -99,18 +95,18 @@ odgs_status check_settings(const odgs_settings* s, odgs_settings* out) {
     if (t.pixels_per_thread == 0 || t.pixels_per_thread_bwd == 0) return ODGS_ERR_INVALID_ARG;
     if (t.batch == 0) t.batch = 128;
     if (t.batch < 1 || t.batch > 256) return ODGS_ERR_INVALID_ARG;
-    if (!finite(t.cov_dilation) || t.cov_dilation < 0.f) return ODGS_ERR_INVALID_ARG;
-    if (!finite(t.r_near) || !(t.r_far > t.r_near) || t.r_near < 0.f) return ODGS_ERR_INVALID_ARG;
+    if (!std::isfinite(t.cov_dilation) || t.cov_dilation < 0.f) return ODGS_ERR_INVALID_ARG;
+    if (!std::isfinite(t.r_near) || !(t.r_far > t.r_near) || t.r_near < 0.f) return ODGS_ERR_INVALID_ARG;
     for (int c = 0; c < 3; ++c)
-        if (!finite(t.bg[c])) return ODGS_ERR_INVALID_ARG;
+        if (!std::isfinite(t.bg[c])) return ODGS_ERR_INVALID_ARG;
     if (t.raw_params != 0 && t.raw_params != 1) return ODGS_ERR_INVALID_ARG;
     if (t.checked != 0 && t.checked != 1) return ODGS_ERR_INVALID_ARG;
     *out = t;
     return ODGS_OK;
 }
 
-odgs_status build_geometry(const odgs_view* views, int n_views, const odgs_settings& s, int n, Geometry* g,
-                           ViewTable* tab) {
+odgs_status odgs::build_geometry(const odgs_view* views, int n_views, const odgs_settings& s, int n, Geometry* g,
+                                 ViewTable* tab) {
     if (!views || n_views < 1 || n_views > kMaxViews || n < 0) return ODGS_ERR_INVALID_ARG;
     long long tiles = 0, pixels = 0, trig = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -118,9 +114,9 @@ odgs_status build_geometry(const odgs_view* views, int n_views, const odgs_setti
         if (w.width < s.tile_w || w.height < 1 || w.width > 16384 || w.height > 16384) return ODGS_ERR_INVALID_ARG;
         if (w.width % s.tile_w != 0) return ODGS_ERR_INVALID_ARG;
         for (int i = 0; i < 9; ++i)
-            if (!finite(w.R_wc[i])) return ODGS_ERR_INVALID_ARG;
+            if (!std::isfinite(w.R_wc[i])) return ODGS_ERR_INVALID_ARG;
         for (int i = 0; i < 3; ++i)
-            if (!finite(w.t_wc[i])) return ODGS_ERR_INVALID_ARG;
+            if (!std::isfinite(w.t_wc[i])) return ODGS_ERR_INVALID_ARG;
         const int tx = w.width / s.tile_w, ty = (w.height + s.tile_h - 1) / s.tile_h;
         ViewDev scratch_view{};
         ViewDev& d = tab ? tab->v[v] : scratch_view;
@@ -149,7 +145,14 @@ odgs_status build_geometry(const odgs_view* views, int n_views, const odgs_setti
     return ODGS_OK;
 }
 
-}  // namespace
+odgs_status odgs::check_gaussians(const odgs_gaussians* g, const odgs_settings& st) {
+    if (!g || g->n < 0) return ODGS_ERR_INVALID_ARG;
+    if (g->n == 0) return ODGS_OK;
+    if (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh) return ODGS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(g->quats) % 16 != 0) return ODGS_ERR_INVALID_ARG;
+    if ((st.sh_coeffs * 3) % 4 == 0 && reinterpret_cast<uintptr_t>(g->sh) % 16 != 0) return ODGS_ERR_INVALID_ARG;
+    return ODGS_OK;
+}
 
 struct odgs_ctx {
     int device = 0, num_sms = 1;
@@ -169,6 +172,8 @@ struct odgs_ctx {
     int stage = 0;
     int launches = 0;
     int bwd_batch = 64;
+    uint32_t wait_limit = kDefaultWaitLimit;
+    int depth_buf = 0, pair_buf = 0;  // which buffer of each double-buffered sort holds its result
 };
 
 extern "C" {
@@ -257,12 +262,8 @@ odgs_status odgs_preprocess(odgs_ctx* c, const odgs_gaussians* g, const odgs_vie
     odgs_settings st;
     odgs_status r = check_settings(s, &st);
     if (r != ODGS_OK) return r;
-    if (g->n < 0) return ODGS_ERR_INVALID_ARG;
-    if (g->n > 0) {
-        if (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh) return ODGS_ERR_INVALID_ARG;
-        if (reinterpret_cast<uintptr_t>(g->quats) % 16 != 0) return ODGS_ERR_INVALID_ARG;
-        if ((st.sh_coeffs * 3) % 4 == 0 && reinterpret_cast<uintptr_t>(g->sh) % 16 != 0) return ODGS_ERR_INVALID_ARG;
-    }
+    r = check_gaussians(g, st);
+    if (r != ODGS_OK) return r;
     ViewTable tab{};
     Geometry geo;
     r = build_geometry(views, n_views, st, g->n, &geo, &tab);
@@ -328,8 +329,10 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     int rb = 0;
     if (launch_radix_sort(dk, dv, &hdr->n_items, c->geo.n_items, 32, reinterpret_cast<uint32_t*>(w + c->L.sort_hist),
                           reinterpret_cast<uint32_t*>(w + c->L.sort_ctr), reinterpret_cast<uint32_t*>(w + c->L.sort_lb),
-                          &hdr->status, c->num_sms, st, &rb, &c->launches) != cudaSuccess)
+                          &hdr->status, c->num_sms, st, &rb, &c->launches, /*hist_ready=*/false,
+                          c->wait_limit) != cudaSuccess)
         return ODGS_ERR_CUDA;
+    c->depth_buf = rb;
     // 2. emit (tile, item) pairs in depth order
     uint8_t* p = c->pb;
     uint32_t* pk[2] = {reinterpret_cast<uint32_t*>(p + c->P.keys0), reinterpret_cast<uint32_t*>(p + c->P.keys1)};
@@ -359,9 +362,11 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     int rp = 0;
     if (launch_radix_sort(pk, pv, &hdr->n_pairs_sort, c->pb_cap, c->geo.key_bits, reinterpret_cast<uint32_t*>(p + c->P.hist),
                           reinterpret_cast<uint32_t*>(p + c->P.ctr), reinterpret_cast<uint32_t*>(p + c->P.lb),
-                          &hdr->status, c->num_sms, st, &rp, &c->launches, /*hist_ready=*/true) != cudaSuccess)
+                          &hdr->status, c->num_sms, st, &rp, &c->launches, /*hist_ready=*/true,
+                          c->wait_limit) != cudaSuccess)
         return ODGS_ERR_CUDA;
     c->sorted_vals = pv[rp];
+    c->pair_buf = rp;
     // 4. per-tile ranges
     if (launch_tile_ranges(pk[rp], hdr, reinterpret_cast<uint2*>(w + c->L.ranges), c->geo.total_tiles, c->pb_cap,
                            c->num_sms, st, &c->launches) != cudaSuccess)
@@ -524,5 +529,52 @@ odgs_status odgs_frame_stats(odgs_ctx* c, odgs_stats* out, void* stream) {
 }
 
 int odgs_last_launch_count(const odgs_ctx* c) { return c ? c->launches : 0; }
+
+odgs_status odgs_set_wait_limit(odgs_ctx* c, uint32_t reads) {
+    if (!c) return ODGS_ERR_INVALID_ARG;
+    c->wait_limit = reads;
+    return ODGS_OK;
+}
+
+odgs_status odgs_debug_screen_grads(odgs_ctx* c, float* out, size_t n_items, void* stream) {
+    if (!c || !out) return ODGS_ERR_INVALID_ARG;
+    if (c->stage < 4) return ODGS_ERR_STATE;
+    if (n_items != c->geo.n_items) return ODGS_ERR_INVALID_ARG;
+    if (n_items == 0) return ODGS_OK;
+    if (cudaMemcpyAsync(out, c->ws + c->L.acc, 3 * sizeof(float4) * n_items, cudaMemcpyDeviceToDevice,
+                        static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return ODGS_ERR_CUDA;
+    return ODGS_OK;
+}
+
+odgs_status odgs_debug_lists(odgs_ctx* c, uint32_t* depth_keys, uint32_t* depth_items, size_t n_items,
+                             uint32_t* pair_tiles, uint32_t* pair_items, size_t n_pairs, uint32_t* ranges,
+                             size_t n_tiles, void* stream) {
+    if (!c) return ODGS_ERR_INVALID_ARG;
+    if (c->stage < 2) return ODGS_ERR_STATE;
+    if ((depth_keys || depth_items) && n_items != c->geo.n_items) return ODGS_ERR_INVALID_ARG;
+    if ((pair_tiles || pair_items) && n_pairs > c->pb_cap) return ODGS_ERR_INVALID_ARG;
+    if (ranges && n_tiles != (size_t)c->geo.total_tiles) return ODGS_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint8_t* w = c->ws;
+    const uint8_t* p = c->pb;
+    const size_t dk = c->depth_buf ? c->L.dkey1 : c->L.dkey0, dv = c->depth_buf ? c->L.dval1 : c->L.dval0;
+    const size_t pk = c->pair_buf ? c->P.keys1 : c->P.keys0, pv = c->pair_buf ? c->P.vals1 : c->P.vals0;
+    struct Copy {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    } copies[5] = {{depth_keys, w + dk, 4 * n_items},
+                   {depth_items, w + dv, 4 * n_items},
+                   {pair_tiles, p ? p + pk : nullptr, 4 * n_pairs},
+                   {pair_items, p ? p + pv : nullptr, 4 * n_pairs},
+                   {ranges, w + c->L.ranges, 8 * n_tiles}};
+    for (const Copy& k : copies) {
+        if (!k.dst || k.bytes == 0) continue;
+        if (!k.src) return ODGS_ERR_STATE;
+        if (cudaMemcpyAsync(k.dst, k.src, k.bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return ODGS_ERR_CUDA;
+    }
+    return ODGS_OK;
+}
 
 }  // extern "C"

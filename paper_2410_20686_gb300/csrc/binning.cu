@@ -41,7 +41,11 @@ __global__ void __launch_bounds__(kScanThreads) k_count_blocks(const uint32_t* _
     unsigned long long c = 0ull;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
         uint32_t k = base + i;
-        if (k < n_items) c += __ldg(&rect[sorted_idx[k]].y);
+        if (k < n_items) {
+            const uint32_t idx = sorted_idx[k];
+            // idx >= n_items only after a depth sort that gave up (status already set)
+            if (idx < n_items) c += __ldg(&rect[idx].y);
+        }
     }
     c = block_sum_u64(c, s);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = c;
@@ -298,7 +302,9 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
     for (int round = 0; round < kScanItems; ++round) {
         const uint32_t k = base + (uint32_t)(round * kScanThreads + tid);
         const uint32_t idx = k < a.n_items ? a.sorted_idx[k] : 0u;
-        const uint4 rc = k < a.n_items ? a.rect[idx] : make_uint4(0u, 0u, 0u, 0u);
+        // an index past the end (only after a depth sort that gave up) emits nothing, as in
+        // k_count_blocks, so that the offsets of the two kernels agree
+        const uint4 rc = (k < a.n_items && idx < a.n_items) ? a.rect[idx] : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t cnt = rc.y;
         // block-wide exclusive scan of the counts of this round (items in depth order)
         unsigned long long x = cnt;

@@ -39,6 +39,20 @@ struct ViewTable {
     uint32_t n_items;
 };
 
+struct Geometry {
+    int total_tiles = 0, total_pixels = 0, total_trig = 0, key_bits = 1;
+    size_t n_items = 0;
+};
+
+// Argument checks shared by every entry point that takes these structs (api.cu): the settings
+// with their defaults filled in, the Gaussian arrays (pointers, 16-byte alignment where the
+// kernels load 16 bytes), and the views (sizes, finite poses, camera model) with the per-view
+// device constants and the frame's tile / pixel totals. ODGS_ERR_INVALID_ARG on any violation.
+odgs_status check_settings(const odgs_settings* s, odgs_settings* out);
+odgs_status check_gaussians(const odgs_gaussians* g, const odgs_settings& st);
+odgs_status build_geometry(const odgs_view* views, int n_views, const odgs_settings& s, int n, Geometry* g,
+                           ViewTable* tab);
+
 struct PreArgs {
     const float *means, *scales, *quats, *opacity, *sh;
     int n, n_views, sh_coeffs;
@@ -141,9 +155,11 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs& a, int sh_degree, cudaStream
 
 int radix_passes(int bits);
 size_t radix_lookback_words(size_t max_items);
+// Look-back reads a sort CTA makes before it gives up and sets kStTimeout (odgs_set_wait_limit).
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
-                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready = false);
+                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit);
 
 int scan_blocks_for(uint32_t n_items);
 cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches);

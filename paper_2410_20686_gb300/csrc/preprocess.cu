@@ -351,6 +351,14 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                     }
                 }
             }
+            if (key == 0xFFFFFFFFu) {
+                // culled: finite records that never pass the alpha test (opacity 0), so that an
+                // index that reaches the blend only through a sort that gave up reads no stale
+                // memory (the colour kernel writes rec_c of the visible items only)
+                a.rec_a[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+                a.rec_b[item] = make_float4(1.f, 0.f, 1.f, 0.f);
+                a.rec_c[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             a.rect[item] = rect;
             a.dkey[item] = key;
             a.dval[item] = (uint32_t)item;
@@ -492,38 +500,68 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         float T[6], TM[6];
         tm_factor(Jm, W, M, T, TM);
         Cov2 c2 = cov2d(TM, a.dilation);
-        const float D = c2.det, iD2 = 1.f / (D * D);
-        const float A = c2.A, B = c2.B, C = c2.C;
+        // conic (C, -B, A) / D -> Sigma_2D -> TM, in the eigenbasis (e1, e2) of Sigma_2D. There
+        // the conic is diag(1 / l1, 1 / l2) and dL/dSigma_2D = -conic G conic is three products, where
+        // G = [[da, db / 2], [db / 2, dc]] is dL/dconic (b the single off-diagonal variable). Formed
+        // in image axes instead, the product loses about eps * cond(Sigma_2D)^2 of relative
+        // precision (cond reaches 1e3 - 1e4 for needle-like Gaussians). l2 = det / l1 uses the
+        // cancellation-free determinant; G is rotated with exact products (float-float), since
+        // e2^T G e2 is a small difference of large terms.
         const float da = g0.z, db = g0.w, dc = g1.x;
-        // conic (C, -B, A) / D -> Sigma_2D, with B the single off-diagonal variable
-        const float dA = (-C * C * da + B * C * db - B * B * dc) * iD2;
-        const float dB = (2.f * B * C * da - (A * C + B * B) * db + 2.f * A * B * dc) * iD2;
-        const float dC = (-B * B * da + A * B * db - A * A * dc) * iD2;
-        // Sigma_2D = TM TM^T: d/dTM_1 = 2 dA TM_1 + dB TM_2, d/dTM_2 = 2 dC TM_2 + dB TM_1
-        float dTM[6];
+        const float hA = 0.5f * (c2.A - c2.C);
+        const float rt = sqrtf(hA * hA + c2.B * c2.B);
+        const float l1 = 0.5f * (c2.A + c2.C) + rt;
+        const float l2 = c2.det / l1;
+        float ex = hA >= 0.f ? hA + rt : c2.B, ey = hA >= 0.f ? c2.B : rt - hA;  // no cancellation
+        const float en = ex * ex + ey * ey;
+        if (en > 0.f) {
+            const float ie = 1.f / sqrtf(en);
+            ex *= ie;
+            ey *= ie;
+        } else {  // isotropic: any basis
+            ex = 1.f;
+            ey = 0.f;
+        }
+        float g11, g12, g22;
+        {
+            const float hb = 0.5f * db;
+            const ff Ge1x = ff_add(two_prod(da, ex), two_prod(hb, ey)), Ge1y = ff_add(two_prod(hb, ex), two_prod(dc, ey));
+            const ff Ge2x = ff_add(two_prod(da, -ey), two_prod(hb, ex)), Ge2y = ff_add(two_prod(hb, -ey), two_prod(dc, ex));
+            g11 = ff_add(ff_mulf(Ge1x, ex), ff_mulf(Ge1y, ey)).hi;
+            g12 = ff_add(ff_mulf(Ge2x, ex), ff_mulf(Ge2y, ey)).hi;
+            g22 = ff_add(ff_mulf(Ge2x, -ey), ff_mulf(Ge2y, ex)).hi;
+        }
+        const float i1 = 1.f / l1, i2 = 1.f / l2;
+        const float s11 = -g11 * i1 * i1, s12 = -g12 * i1 * i2, s22 = -g22 * i2 * i2;
+        // rows of TM and T in the eigenbasis; Sigma_2D = TM TM^T + delta I gives
+        // dL/dTM' = 2 dSigma' TM' (rows dr1, dr2)
+        float dr1[3], dr2[3], t1[3], t2[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            dTM[k] = 2.f * dA * TM[k] + dB * TM[3 + k];
-            dTM[3 + k] = 2.f * dC * TM[3 + k] + dB * TM[k];
+            const float r1 = ex * TM[k] + ey * TM[3 + k], r2 = ex * TM[3 + k] - ey * TM[k];
+            dr1[k] = 2.f * (s11 * r1 + s12 * r2);
+            dr2[k] = 2.f * (s12 * r1 + s22 * r2);
+            t1[k] = ex * T[k] + ey * T[3 + k];
+            t2[k] = ex * T[3 + k] - ey * T[k];
         }
-        // TM = T M: dT = dTM M^T, dM += T^T dTM
-        float dT[6];
+        // TM = T M: dM += T'^T dTM' (the rotation cancels), dT' = dTM' M^T
+        float dT1[3], dT2[3];
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-                dT[3 * i + j] = dTM[3 * i] * M[3 * j] + dTM[3 * i + 1] * M[3 * j + 1] + dTM[3 * i + 2] * M[3 * j + 2];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) dM[3 * j + k] += T[j] * dTM[k] + T[3 + j] * dTM[3 + k];
-        // T = J W: dJ = dT W^T
+            for (int k = 0; k < 3; ++k) dM[3 * j + k] += t1[j] * dr1[k] + t2[j] * dr2[k];
+            dT1[j] = dr1[0] * M[3 * j] + dr1[1] * M[3 * j + 1] + dr1[2] * M[3 * j + 2];
+            dT2[j] = dr2[0] * M[3 * j] + dr2[1] * M[3 * j + 1] + dr2[2] * M[3 * j + 2];
+        }
+        // T = J W: dJ' = dT' W^T, then back to image axes: dJ = [e1 e2] dJ'
         float dJ[6];
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                dJ[3 * i + j] = dT[3 * i] * W[3 * j] + dT[3 * i + 1] * W[3 * j + 1] + dT[3 * i + 2] * W[3 * j + 2];
+        for (int j = 0; j < 3; ++j) {
+            const float p1 = dT1[0] * W[3 * j] + dT1[1] * W[3 * j + 1] + dT1[2] * W[3 * j + 2];
+            const float p2 = dT2[0] * W[3 * j] + dT2[1] * W[3 * j + 1] + dT2[2] * W[3 * j + 2];
+            dJ[j] = ex * p1 - ey * p2;
+            dJ[3 + j] = ey * p1 + ex * p2;
+        }
         // dL/dt: mean path d(u, v)/dt = J (Eq. 10 for ERP) plus J's dependence on t
         const float fx = V.fx, fy = V.fy;
         float dtx, dty, dtz;

@@ -9,8 +9,10 @@
 // pass is then one "onesweep" kernel (Adinets & Merrill 2022): a CTA ranks a 2048- or 4096-key
 // tile in shared memory (warp-level ranking by ballots or a match keeps it stable), publishes its per-digit counts,
 // obtains the exclusive prefix of all earlier tiles by decoupled look-back, and writes its keys
-// digit-run by digit-run (coalesced). Look-back waits are bounded: a CTA that gives up sets
-// kStTimeout in the status word and returns.
+// digit-run by digit-run (coalesced). Look-back waits are bounded: a CTA that has read the
+// look-back words `wait_limit` times without reaching an inclusive prefix sets kStTimeout in the
+// status word and finishes with a partial prefix; its out-of-range writes are skipped, and every
+// consumer of the sorted arrays bounds the indices it reads.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
@@ -24,7 +26,6 @@ constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
-constexpr uint32_t kSpinLimit = 1u << 22;
 
 __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
                                                     int begin_bit, int n_passes, uint32_t* __restrict__ hist) {
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint32_t* __
                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          const uint32_t* __restrict__ n_ptr, int shift,
                                                          int bits, int use_match, const uint32_t* __restrict__ hist,
-                                                         uint32_t* lookback, uint32_t* tile_ctr, uint32_t* status) {
+                                                         uint32_t* lookback, uint32_t* tile_ctr, uint32_t* status,
+                                                         uint32_t wait_limit) {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_warp_hist[kSortWarps][kRadix];
     __shared__ uint32_t s_digit_excl[kRadix];
@@ -176,15 +178,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint32_t* __
     uint32_t excl = 0;
     if (tile > 0) {
         int j = (int)tile - 1;
-        uint32_t spins = 0;
+        uint32_t reads = 0;
         while (j >= 0) {
+            if (reads++ >= wait_limit) {  // every read counts, so a limit of 0 gives up at once
+                atomicOr(status, kStTimeout);
+                break;
+            }
             const uint32_t e = ld_volatile(lookback + (size_t)j * kRadix + tid);
             const uint32_t flag = e & ~kCountMask;
             if (flag == 0u) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(status, kStTimeout);
-                    break;
-                }
                 __nanosleep(32);
                 continue;
             }
@@ -234,7 +236,7 @@ size_t radix_lookback_words(size_t max_items) {
 // hist_ready the digit histograms of all passes are already in hist (counted by the producer).
 cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
-                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready) {
+                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit) {
     const int passes = radix_passes(bits);
     *result_buf = 0;
     if (passes == 0 || max_items == 0) return cudaSuccess;
@@ -268,11 +270,11 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
         if (large)
             k_onesweep<kSortItemsMax><<<max(tiles, 1), kSortThreads, 0, st>>>(
                 k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
-                hist + p * kRadix, lookback, tile_ctrs + p, status);
+                hist + p * kRadix, lookback, tile_ctrs + p, status, wait_limit);
         else
             k_onesweep<kSortItemsMax / 2><<<max(tiles, 1), kSortThreads, 0, st>>>(
                 k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
-                hist + p * kRadix, lookback, tile_ctrs + p, status);
+                hist + p * kRadix, lookback, tile_ctrs + p, status, wait_limit);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
         cur ^= 1;

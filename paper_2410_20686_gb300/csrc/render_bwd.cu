@@ -109,6 +109,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
         const bool inside = y < V.H;
         const float fi0 = (float)xp, fj = (float)y;
         const uint2 rg = a.ranges[item];
+        // entries past the tile's range (possible only when the lists were rebuilt after a sort
+        // that gave up, so that they differ from the forward's) stage as never-blending entries
+        const uint32_t rlen = rg.y > rg.x ? rg.y - rg.x : 0u;
         const int wr0 = ty * a.tile_h + wy0, wr1 = ty * a.tile_h + wy1;
 
         float T[PPT], Bg[PPT], g0[PPT], g1[PPT], g2[PPT];
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
             const int cnt = hi - lo;
             int split = 0;
             for (int j = tid; j < cnt; j += nthr) {
-                const uint32_t idx = a.pair_vals[rg.x + lo + j];
+                const uint32_t idx = (uint32_t)(lo + j) < rlen ? a.pair_vals[rg.x + lo + j] : 0xFFFFFFFFu;
                 float4 ra, rb, rc;
                 gather_records(a.rec_a, a.rec_b, a.rec_c, idx, a.n_items, ra, rb, rc);
                 Staged s = stage_entry(ra, rb, rc, x0, tw, V.W, V.model == 0);

@@ -56,53 +56,32 @@ inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odgs_view* view,
                                               const odgs_settings* s, float* image, float* final_T,
                                               uint32_t* status_out, void* stream) {
-    // ---- arguments (nothing is launched when one is rejected)
-    if (!g || !view || !s || !image || !status_out) return ODGS_ERR_INVALID_ARG;
-    if (g->n < 0 || g->n > kStaticMaxGaussians) return ODGS_ERR_INVALID_ARG;
+    // ---- arguments (nothing is launched when one is rejected): the checks of the workspace
+    // entry points, then this entry point's own size limits
+    if (!view || !image || !status_out) return ODGS_ERR_INVALID_ARG;
+    odgs_settings st;
+    odgs_status r = check_settings(s, &st);
+    if (r != ODGS_OK) return r;
+    r = check_gaussians(g, st);
+    if (r != ODGS_OK) return r;
+    if (g->n > kStaticMaxGaussians) return ODGS_ERR_INVALID_ARG;
     if ((long long)view->width * view->height > kStaticMaxPixels) return ODGS_ERR_INVALID_ARG;
-    if (view->width > 16384 || view->height > 16384) return ODGS_ERR_INVALID_ARG;
-    if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh)) return ODGS_ERR_INVALID_ARG;
-    if (g->n > 0 && reinterpret_cast<uintptr_t>(g->quats) % 16 != 0) return ODGS_ERR_INVALID_ARG;
-    odgs_settings st = *s;
-    if (st.tile_w == 0 && st.tile_h == 0) { st.tile_w = 16; st.tile_h = 16; }
-    if (st.batch == 0) st.batch = 128;
-    if (st.sh_degree < 0 || st.sh_degree > 3 || st.sh_coeffs < (st.sh_degree + 1) * (st.sh_degree + 1) ||
-        st.sh_coeffs > 64)
-        return ODGS_ERR_INVALID_ARG;
-    if (g->n > 0 && (st.sh_coeffs * 3) % 4 == 0 && reinterpret_cast<uintptr_t>(g->sh) % 16 != 0)
-        return ODGS_ERR_INVALID_ARG;
-    if (!(st.tile_w == 8 || st.tile_w == 16 || st.tile_w == 32) || st.tile_h < 1 ||
-        st.tile_w * st.tile_h < 32 || st.tile_w * st.tile_h > 1024 || (st.tile_w * st.tile_h) % 32 != 0)
-        return ODGS_ERR_INVALID_ARG;
-    st.pixels_per_thread = pixels_per_thread(st.tile_w, st.tile_h, st.pixels_per_thread, 2);
-    if (st.pixels_per_thread == 0) return ODGS_ERR_INVALID_ARG;
-    if (st.batch < 1 || st.batch > 256) return ODGS_ERR_INVALID_ARG;
-    if (!(st.cov_dilation >= 0.f) || !(st.r_near >= 0.f) || !(st.r_far > st.r_near)) return ODGS_ERR_INVALID_ARG;
+    ViewTable tab{};
+    Geometry geo;
+    r = build_geometry(view, 1, st, g->n, &geo, &tab);
+    if (r != ODGS_OK) return r;
     const int W = view->width, H = view->height;
-    if (W < st.tile_w || H < 1 || W % st.tile_w != 0 || W > 65535 || H > 65535) return ODGS_ERR_INVALID_ARG;
 
     uint8_t* base = nullptr;
-    odgs_status r = scratch_for_current_device(&base);
+    r = scratch_for_current_device(&base);
     if (r != ODGS_OK) return r;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     int num_sms = 1, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return ODGS_ERR_CUDA;
-
-    // ---- view table (one view)
-    ViewTable tab{};
-    ViewDev& V = tab.v[0];
-    V.W = W; V.H = H;
-    V.tiles_x = W / st.tile_w;
-    V.tiles_y = (H + st.tile_h - 1) / st.tile_h;
-    V.tile_base = 0; V.pix_base = 0; V.trig_u = 0; V.trig_v = W;
-    if (!fill_camera(*view, V)) return ODGS_ERR_INVALID_ARG;
-    tab.n_views = 1;
-    tab.n_items = (uint32_t)g->n;
-    const int tiles = V.tiles_x * V.tiles_y;
-    int key_bits = 1;
-    while ((1 << key_bits) < tiles) ++key_bits;
+    const int tiles = geo.total_tiles;
+    const int key_bits = geo.key_bits;
     const size_t n = (size_t)g->n, pixels = (size_t)W * H;
 
     // ---- carve the static array
@@ -146,7 +125,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
 
     // ---- the forward path (same kernels as the workspace entry points)
     int launches = 0;
-    if (launch_setup(tab, vd, trig, hdr, W + H, strm) != cudaSuccess) return ODGS_ERR_CUDA;
+    if (launch_setup(tab, vd, trig, hdr, geo.total_trig, strm) != cudaSuccess) return ODGS_ERR_CUDA;
     PreArgs a{};
     a.means = g->means; a.scales = g->scales; a.quats = g->quats; a.opacity = g->opacity; a.sh = g->sh;
     a.n = g->n; a.n_views = 1; a.sh_coeffs = st.sh_coeffs;
@@ -162,7 +141,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     if (launch_preprocess(a, st.sh_degree, strm) != cudaSuccess) return ODGS_ERR_CUDA;
     int rb = 0;
     if (launch_radix_sort(dk, dv, &hdr->n_items, n, 32, d_hist, d_ctr, d_lb, &hdr->status, num_sms, strm, &rb,
-                          &launches) != cudaSuccess)
+                          &launches, /*hist_ready=*/false, kDefaultWaitLimit) != cudaSuccess)
         return ODGS_ERR_CUDA;
     BinArgs b{};
     b.sorted_idx = dv[rb]; b.rect = rect; b.rect2 = rect2; b.views = vd; b.n_per_view = g->n > 0 ? g->n : 1;
@@ -174,7 +153,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     if (launch_binning(b, strm, &launches) != cudaSuccess) return ODGS_ERR_CUDA;
     int rp = 0;
     if (launch_radix_sort(pk, pv, &hdr->n_pairs_sort, cap, key_bits, p_hist, p_ctr, p_lb, &hdr->status, num_sms,
-                          strm, &rp, &launches, /*hist_ready=*/true) != cudaSuccess)
+                          strm, &rp, &launches, /*hist_ready=*/true, kDefaultWaitLimit) != cudaSuccess)
         return ODGS_ERR_CUDA;
     if (launch_tile_ranges(pk[rp], hdr, ranges, tiles, cap, num_sms, strm, &launches) != cudaSuccess)
         return ODGS_ERR_CUDA;

@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes as C
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -231,6 +232,37 @@ class Rasterizer:
         stream = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
         L.check(self.lib.odgs_get_status(self.ctx, C.byref(bits), stream), "odgs_get_status")
         return int(bits.value)
+
+    def set_wait_limit(self, reads: int):
+        """Bound of the sorts' look-back waits from the next bin_sort (0: give up at once)."""
+        L.check(self.lib.odgs_set_wait_limit(self.ctx, int(reads)), "odgs_set_wait_limit")
+
+    def debug_lists(self) -> dict:
+        """Copies of the frame's depth order, tile-sorted pairs and tile ranges (uint32 tensors;
+        synchronises the stream once to read the number of sorted pairs)."""
+        n_items = int(self._keep[0].shape[0]) * self.n_views
+        s = self.settings
+        n_tiles = sum((v.width // s.tile_w) * ((v.height + s.tile_h - 1) // s.tile_h) for v in self.views)
+        n_pairs = self.stats()["pairs_sorted"]
+        u32 = dict(dtype=torch.int32, device=self.device)
+        out = dict(depth_keys=torch.empty(n_items, **u32), depth_items=torch.empty(n_items, **u32),
+                   pair_tiles=torch.empty(n_pairs, **u32), pair_items=torch.empty(n_pairs, **u32),
+                   ranges=torch.empty((n_tiles, 2), **u32))
+        stream = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        L.check(self.lib.odgs_debug_lists(self.ctx, _ptr(out["depth_keys"]), _ptr(out["depth_items"]), n_items,
+                                          _ptr(out["pair_tiles"]), _ptr(out["pair_items"]), n_pairs,
+                                          _ptr(out["ranges"]), n_tiles, stream), "odgs_debug_lists")
+        torch.cuda.current_stream(self.device).synchronize()
+        return {k: v.cpu().numpy().view(np.uint32) for k, v in out.items()}
+
+    def debug_screen_grads(self):
+        """The last backward blend's per-(view, Gaussian) screen-space gradients, [views * n, 9]
+        float32 (dL/du, dL/dv, dL/da, dL/db, dL/dc, dL/do, dL/dr, dL/dg, dL/db)."""
+        n_items = int(self._keep[0].shape[0]) * self.n_views
+        out = torch.empty((n_items, 12), dtype=torch.float32, device=self.device)
+        stream = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        L.check(self.lib.odgs_debug_screen_grads(self.ctx, _ptr(out), n_items, stream), "odgs_debug_screen_grads")
+        return out[:, :9].cpu().numpy()
 
     def launch_count(self) -> int:
         return int(self.lib.odgs_last_launch_count(self.ctx))

@@ -13,6 +13,11 @@ EPS_SKIP = 2e-5
 EPS_TERM = 1e-4
 EPS_CLAMP = 2e-5
 GRAD_TOL = 1e-3
+# element-wise gradient band: |g - g_ref| <= GRAD_BAND * (|g_ref| + GRAD_FLOOR * max|g_ref|), per
+# tensor, for every element (no fraction may fall outside)
+GRAD_BAND = 1e-3
+GRAD_FLOOR = 1e-3
+GRAD_NAMES = ("means", "scales", "quats", "opacity", "sh")
 
 
 def oracle_settings(rs, deg=None):
@@ -61,3 +66,23 @@ def rel_l2(a, b):
     b = np.asarray(b, np.float64).ravel()
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def assert_grads_close(gpu, ref, names=GRAD_NAMES, tol=GRAD_TOL):
+    """Gradient parity per parameter tensor: relative L2 error <= tol and every element within
+    GRAD_BAND * (|g_ref| + GRAD_FLOOR * max|g_ref|). The message names the worst element."""
+    for k in names:
+        g = np.asarray(gpu[k], np.float64).ravel()
+        r = np.asarray(ref[k], np.float64).ravel()
+        e = rel_l2(g, r)
+        assert e <= tol, f"{k}: relative L2 error {e:.3e}"
+        if r.size == 0:
+            continue
+        lim = GRAD_BAND * (np.abs(r) + GRAD_FLOOR * np.abs(r).max())
+        d = np.abs(g - r)
+        bad = d > lim
+        if bad.any():
+            i = int(np.argmax(np.where(lim > 0, d / np.where(lim > 0, lim, 1.0), np.inf * (d > 0))))
+            raise AssertionError(
+                f"{k}: {int(bad.sum())} of {bad.size} elements outside the element-wise band; worst index {i}: "
+                f"gpu {g[i]:.9e} ref {r[i]:.9e} |d| {d[i]:.3e} > band {lim[i]:.3e} (max|ref| {np.abs(r).max():.3e})")

@@ -193,3 +193,55 @@ def test_paper_hyperparameters_are_the_defaults():
     p = DensifyParams()
     assert (p.tau_min, p.tau_max, p.percent_dense) == (D.TAU_MIN, D.TAU_MAX, D.PERCENT_DENSE)
     assert vals["densify_until_iter"] < vals["iterations"]
+
+
+@pytest.mark.parametrize("raw", [False, True])
+def test_float32_selection_equals_the_fp64_rule_wherever_rounding_cannot_decide(raw):
+    """``select`` decides in float32 (the kernel's precision, so that the GPU's decisions can be
+    compared bit for bit); here it is pinned to the FP64 rule of Sec. 3.3 / App. A.1 applied to
+    the same stored statistics: densify when the mean gradient reaches tau_mu at the mean
+    1 - cos theta, clone when the largest scale is at most percent_dense x extent (split
+    otherwise), prune below min_opacity or above max_scale. Every case whose FP64 margin exceeds
+    float32 rounding (a relative 1e-5) must agree; near-threshold cases are drawn on purpose."""
+    rng = np.random.default_rng(17 + raw)
+    n = 400_000
+    prm = D.DensifyParams(scene_extent=3.0, min_opacity=0.005, max_scale=0.05, raw_params=raw)
+    count = rng.integers(0, 6, n).astype(np.uint32)
+    emean = rng.uniform(0.0, 1.0, n)
+    tau64 = D.tau(emean)
+    # a third of the means straddle their threshold by under 1e-4 relative
+    ratio = np.where(rng.uniform(size=n) < 0.33, 1.0 + rng.uniform(-1e-4, 1e-4, n), rng.uniform(0.2, 3.0, n))
+    grad = (tau64 * ratio * count).astype(np.float32)
+    elev = (emean * count).astype(np.float32)
+    smax_target = np.where(rng.uniform(size=n) < 0.3, 3e-3 * (1 + rng.uniform(-1e-4, 1e-4, n)),
+                           rng.uniform(5e-4, 0.08, n))
+    scales = (smax_target[:, None] * rng.uniform(0.2, 1.0, (n, 3))).astype(np.float64)
+    scales[np.arange(n), rng.integers(0, 3, n)] = smax_target
+    opacity = np.where(rng.uniform(size=n) < 0.2, 0.005 * (1 + rng.uniform(-1e-4, 1e-4, n)), rng.uniform(1e-3, 1, n))
+    s32 = (np.log(scales) if raw else scales).astype(np.float32)
+    o32 = (np.log(opacity / (1 - opacity)) if raw else opacity).astype(np.float32)
+    act = D.select(grad, elev, count, s32, o32, prm)
+
+    # the FP64 rule on the stored (float32) values
+    s64 = np.exp(s32.astype(np.float64)) if raw else s32.astype(np.float64)
+    o64 = 1.0 / (1.0 + np.exp(-o32.astype(np.float64))) if raw else o32.astype(np.float64)
+    seen = count > 0
+    c = np.maximum(count, 1).astype(np.float64)
+    g = grad.astype(np.float64) / c
+    t = D.tau(elev.astype(np.float64) / c)
+    smax = s64.max(axis=1)
+    big_thr = prm.percent_dense * prm.scene_extent
+    hot = seen & (g >= t)
+    prune = (o64 < prm.min_opacity) | (smax > prm.max_scale)
+    rule = np.where(prune, D.PRUNE, np.where(hot, np.where(smax > big_thr, D.SPLIT, D.CLONE), D.KEEP))
+    # decisions float32 rounding can flip: any compared quantity within 1e-5 relative of its threshold
+    eps = 1e-5
+    near = seen & (np.abs(g - t) <= eps * t)
+    near |= np.abs(smax - big_thr) <= eps * big_thr
+    near |= np.abs(smax - prm.max_scale) <= eps * prm.max_scale
+    near |= np.abs(o64 - prm.min_opacity) <= eps * prm.min_opacity
+    assert near.mean() < 0.5 and (~near).sum() > 100_000
+    assert np.array_equal(act[~near], rule[~near]), np.nonzero(act[~near] != rule[~near])[0][:5]
+    # every kind of decision is exercised
+    for a in (D.KEEP, D.CLONE, D.SPLIT, D.PRUNE):
+        assert (rule[~near] == a).sum() > 1000

@@ -548,3 +548,21 @@ def test_eq12_first_row_agrees_and_second_row_is_sign_flipped():
         for (i, j), coef in c[k].items():
             sign = 1.0 if i == 0 else -1.0
             np.testing.assert_allclose(dJ[i, j], sign * coef, rtol=1e-6, atol=1e-6 * abs(coef) + 1e-9)
+
+
+def test_chain_alone_reproduces_the_adjoint_from_its_screen_space_gradients():
+    """orc_chain (the chain rule of App. A.3 applied to given screen-space gradients) is the second
+    half of orc_backward: fed orc_backward's own screen-space gradients it returns the same
+    parameter gradients, and fed zeros it returns zeros."""
+    sc = S.random_scene(60, 64, 32, seed=13, sh_degree=2, log_scale=(-2.5, 0.6))
+    p = O.Params.of(sc)
+    st = O.Settings(sh_degree=2)
+    v = S.yaw_view(64, 32, (0.1, 0.0, -0.2), 0.7)
+    w = np.random.default_rng(13).normal(size=(3, 32, 64))
+    full = O.backward(p, v, st, w, want_g2=True)
+    assert np.abs(full["screen"]).max() > 0
+    part = O.chain(p, v, st, full["screen"])
+    for k in ("means", "scales", "quats", "opacity", "sh"):
+        assert np.array_equal(part[k], full[k]), k
+    zero = O.chain(p, v, st, np.zeros((p.n, 9)))
+    assert all(not np.any(zero[k]) for k in zero)

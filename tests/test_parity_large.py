@@ -9,7 +9,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2410_20686_gb300 import scenes as S
-from tests.helpers import EPS_CLAMP, EPS_SKIP, EPS_TERM, compare_image, oracle_settings, rel_l2
+from tests.helpers import EPS_CLAMP, EPS_SKIP, EPS_TERM, assert_grads_close, compare_image, oracle_settings
 
 pytestmark = pytest.mark.gpu
 NAMES = ("means", "scales", "quats", "opacity", "sh")
@@ -29,10 +29,8 @@ def _masked_weights(p, view, st, pix, seed):
     return g, full.reshape(3, view.height, view.width)
 
 
-def _assert_grads(gpu, ref, tol=1e-3):
-    for k in NAMES:
-        e = rel_l2(gpu[k], ref[k])
-        assert e <= tol, f"{k}: relative L2 error {e:.3e}"
+def _assert_grads(gpu, ref):
+    assert_grads_close(gpu, ref, NAMES)
 
 
 def test_config2_sampled_images_and_gradients():
@@ -41,7 +39,7 @@ def test_config2_sampled_images_and_gradients():
     sc = S.config2()
     rs = _rs(sh_degree=3)
     v = sc.views[0]
-    pix = S.sample_pixels(v.width, v.height, 768, S.stress_tiles(v.width, v.height)[:3], seed=22)
+    pix = S.sample_pixels(v.width, v.height, 1024, S.stress_tiles(v.width, v.height), seed=22)
     p = O.Params.of(sc)
     st = oracle_settings(rs)
     params = [torch.tensor(a, device="cuda") for a in (sc.means, sc.scales, sc.quats, sc.opacity, sc.sh)]
@@ -67,19 +65,18 @@ def test_config3_all_views_in_one_frame():
     imgs, _ = rast.forward(*params, sc.views, rs, want_T=False)
     p = O.Params.of(sc)
     st = oracle_settings(rs)
-    checked = [0, 5, 12]  # one view of each resolution
-    weights, refs = [], []
-    for i in range(len(sc.views)):
-        v = sc.views[i]
-        if i in checked:
-            pix = S.sample_pixels(v.width, v.height, 384, S.stress_tiles(v.width, v.height)[:1], seed=30 + i)
-            col, _, _, margins = O.render(p, v, st, pix=pix)
-            compare_image(imgs[i].cpu().numpy().astype(np.float64).reshape(3, -1)[:, pix].T, col, margins)
-            g, full = _masked_weights(p, v, st, pix, 30 + i)
-            refs.append(O.backward(p, v, st, g, pix=pix))
-            weights.append(torch.tensor(full, device="cuda"))
-        else:
-            weights.append(torch.zeros((3, v.height, v.width), device="cuda"))
+    weights, refs, amb = [], [], []
+    for i, v in enumerate(sc.views):  # every view: 128 random pixels plus one pole or seam tile each
+        stress = S.stress_tiles(v.width, v.height)
+        pix = S.sample_pixels(v.width, v.height, 128, [stress[i % len(stress)]], seed=30 + i)
+        col, _, _, margins = O.render(p, v, st, pix=pix)
+        # a view's sample is small (one ambiguous pixel is ~0.3 %): the fraction is bounded over the frame
+        compare_image(imgs[i].cpu().numpy().astype(np.float64).reshape(3, -1)[:, pix].T, col, margins, max_amb_frac=1.0)
+        amb.append(O.ambiguous(margins, EPS_SKIP, EPS_TERM))
+        g, full = _masked_weights(p, v, st, pix, 30 + i)
+        refs.append(O.backward(p, v, st, g, pix=pix))
+        weights.append(torch.tensor(full, device="cuda"))
+    assert np.concatenate(amb).mean() <= 2e-3
     gpu = rast.backward(weights)
     torch.cuda.synchronize()
     assert rast.status() == 0
@@ -95,17 +92,14 @@ def test_config4_grouped_frame_with_recomputed_lists():
     params = [torch.tensor(a, device="cuda") for a in (sc.means, sc.scales, sc.quats, sc.opacity, sc.sh)]
     p = O.Params.of(sc)
     st = oracle_settings(rs)
-    checked = [1, 6]
     weights, refs, samples = [], [], {}
-    for i, v in enumerate(sc.views):
-        if i in checked:
-            pix = S.sample_pixels(v.width, v.height, 160, [], seed=40 + i)
-            g, full = _masked_weights(p, v, st, pix, 40 + i)
-            refs.append(O.backward(p, v, st, g, pix=pix))
-            weights.append(torch.tensor(full, device="cuda"))
-            samples[i] = pix
-        else:
-            weights.append(torch.zeros((3, v.height, v.width), device="cuda"))
+    for i, v in enumerate(sc.views):  # every view: 96 random pixels plus one pole or seam tile each
+        stress = S.stress_tiles(v.width, v.height)
+        pix = S.sample_pixels(v.width, v.height, 96, [stress[i % len(stress)]], seed=40 + i)
+        g, full = _masked_weights(p, v, st, pix, 40 + i)
+        refs.append(O.backward(p, v, st, g, pix=pix))
+        weights.append(torch.tensor(full, device="cuda"))
+        samples[i] = pix
 
     def fixed_weights(images, targets):  # linear loss: dL/dC = weights
         return None, weights
@@ -114,9 +108,12 @@ def test_config4_grouped_frame_with_recomputed_lists():
     gf.step()
     torch.cuda.synchronize()
     assert gf.status() == 0
-    for i in checked:
-        v = sc.views[i]
+    amb = []
+    for i, v in enumerate(sc.views):
         col, _, _, margins = O.render(p, v, st, pix=samples[i])
-        compare_image(gf.images[i].cpu().numpy().astype(np.float64).reshape(3, -1)[:, samples[i]].T, col, margins)
+        compare_image(gf.images[i].cpu().numpy().astype(np.float64).reshape(3, -1)[:, samples[i]].T, col, margins,
+                      max_amb_frac=1.0)
+        amb.append(O.ambiguous(margins, EPS_SKIP, EPS_TERM))
+    assert np.concatenate(amb).mean() <= 2e-3
     ref = {k: sum(r[k] for r in refs) for k in NAMES}
     _assert_grads({k: t.cpu().numpy().astype(np.float64) for k, t in gf.grads.items()}, ref)

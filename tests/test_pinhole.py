@@ -7,7 +7,7 @@ from scipy.spatial.transform import Rotation
 
 from oracle import oracle as O
 from paper_2410_20686_gb300 import scenes as S
-from tests.helpers import EPS_CLAMP, EPS_SKIP, EPS_TERM, GRAD_TOL, compare_image, oracle_settings, rel_l2, to_torch
+from tests.helpers import EPS_CLAMP, EPS_SKIP, EPS_TERM, assert_grads_close, compare_image, oracle_settings, to_torch
 
 pytestmark = pytest.mark.gpu
 NAMES = ("means", "scales", "quats", "opacity", "sh")
@@ -48,9 +48,7 @@ def test_pinhole_forward_and_backward_match_the_oracle():
     torch.cuda.synchronize()
     assert rast.status() == 0
     ref = O.backward(p, v, st, w)
-    for k in NAMES:
-        e = rel_l2(g[k].cpu().numpy().astype(np.float64), ref[k])
-        assert e <= GRAD_TOL, f"{k}: relative L2 error {e:.3e}"
+    assert_grads_close({k: g[k].cpu().numpy().astype(np.float64) for k in NAMES}, ref, NAMES)
 
 
 def test_cubemap_faces_in_one_frame():
@@ -91,8 +89,7 @@ def test_mixed_erp_and_pinhole_views_in_one_frame():
     for v, w in zip(sc.views, ws):
         r = O.backward(p, v, st, w)
         ref = r if ref is None else {k: ref[k] + r[k] for k in NAMES}
-    for k in NAMES:
-        assert rel_l2(g[k].cpu().numpy().astype(np.float64), ref[k]) <= GRAD_TOL, k
+    assert_grads_close({k: g[k].cpu().numpy().astype(np.float64) for k in NAMES}, ref, NAMES)
 
 
 def test_pinhole_images_do_not_depend_on_the_tiling():

@@ -8,8 +8,7 @@ from oracle import densify as OD
 from oracle import oracle as O
 from oracle import train as OT
 from paper_2410_20686_gb300 import scenes as S
-from tests.helpers import (EPS_CLAMP, EPS_SKIP, EPS_TERM, GRAD_TOL, IMG_TOL, compare_image, oracle_settings,
-                           rel_l2)
+from tests.helpers import EPS_CLAMP, EPS_SKIP, EPS_TERM, IMG_TOL, assert_grads_close, compare_image, oracle_settings
 
 pytestmark = pytest.mark.gpu
 NAMES = ("means", "scales", "quats", "opacity", "sh")
@@ -76,9 +75,7 @@ def test_raw_parameters_render_and_differentiate_like_the_activated_oracle():
     compare_image(imgs[0].cpu().numpy().astype(np.float64), col, margins, tol=IMG_TOL)
     ref = O.backward(p, v, st, w)
     ref["scales"], ref["opacity"] = OT.chain(log_s, logit, ref["scales"], ref["opacity"])
-    for k in NAMES:
-        e = rel_l2(g[k].cpu().numpy().astype(np.float64), ref[k])
-        assert e <= GRAD_TOL, f"{k}: relative L2 error {e:.3e}"
+    assert_grads_close({k: g[k].cpu().numpy().astype(np.float64) for k in NAMES}, ref, NAMES)
 
 
 def test_densification_on_raw_parameters_matches_the_oracle():
