@@ -231,8 +231,10 @@ odgs_status odgs_debug_lists(odgs_ctx *ctx, uint32_t *depth_keys, uint32_t *dept
  * odgs_render_bwd, for tests and inspection (the reverse of Eq. 2-3 before the chain rule of
  * App. A.3). Asynchronous device-to-device copy on `stream` into out: device float32
  * [n_items][12], n_items = views * n, item = view * n + Gaussian, per item
- *   dL/du, dL/dv (ERP mean, pixels), dL/da, dL/db, dL/dc (conic, power = ln o - (a dx^2 +
- *   2 b dx dy + c dy^2) / 2), dL/do (opacity), dL/dr, dL/dg, dL/db (colour), 0, 0, 0.
+ *   dL/du, dL/dv (ERP mean, pixels), dL/da, dL/dbeta, dL/dgamma (the conic in slice form:
+ *   power = ln o - (a t^2 + gamma dy^2) / 2 with t = dx - beta dy; with Sigma_2D = [[A, B],
+ *   [B, C]], a = C / det, beta = B / C, gamma = 1 / C, so that the conic's entries are a,
+ *   -a beta, gamma + a beta^2), dL/do (opacity), dL/dr, dL/dg, dL/db (colour), 0, 0, 0.
  * ODGS_ERR_STATE before odgs_render_bwd; ODGS_ERR_INVALID_ARG if n_items differs. */
 odgs_status odgs_debug_screen_grads(odgs_ctx *ctx, float *out, size_t n_items, void *stream);
 

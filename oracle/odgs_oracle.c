@@ -514,9 +514,17 @@ static void atomic_add(double *p, double x)
     *p += x;
 }
 
-/* Reverse pass of Eq. 3 at one pixel: accumulates dL/d(u, v, conic, opacity, rgb). */
+/* Reverse pass of Eq. 3 at one pixel: accumulates dL/d(u, v, conic, opacity, rgb). With g2abs
+ * non-NULL it also accumulates the absolute value of every pixel's contribution, the magnitude
+ * that bounds the rounding error of any finite-precision evaluation of the same sums. */
+static void add_contrib(double *acc, double *abs_acc, int c, double x)
+{
+    atomic_add(&acc[c], x);
+    if (abs_acc) atomic_add(&abs_acc[c], fabs(x));
+}
+
 static void blend_pixel_adjoint(const sorted_g *g, int m, double px, double py, int W,
-                                const orc_settings *s, const double *dLdC, double *g2,
+                                const orc_settings *s, const double *dLdC, double *g2, double *g2abs,
                                 contrib *list, int cap)
 {
     double out[3], Tf;
@@ -529,23 +537,24 @@ static void blend_pixel_adjoint(const sorted_g *g, int m, double px, double py, 
         const sorted_g *gk = &g[e->k];
         double a = e->alpha, T = e->T;
         double *acc = g2 + (size_t)G2_N * gk->id;
+        double *aab = g2abs ? g2abs + (size_t)G2_N * gk->id : NULL;
         /* dC/drgb = alpha T */
-        for (int c = 0; c < 3; ++c) atomic_add(&acc[G2_R + c], dLdC[c] * a * T);
+        for (int c = 0; c < 3; ++c) add_contrib(acc, aab, G2_R + c, dLdC[c] * a * T);
         /* dC/dalpha = rgb T - B / (1 - alpha) */
         double dLda = 0.0;
         for (int c = 0; c < 3; ++c) dLda += dLdC[c] * (gk->rgb[c] * T - Bk[c] / (1.0 - a));
         for (int c = 0; c < 3; ++c) Bk[c] += gk->rgb[c] * a * T;
         if (e->clamped) continue; /* alpha = 0.99 does not depend on o or G */
         /* alpha = o G, G = exp(power) */
-        atomic_add(&acc[G2_O], dLda * e->G);
+        add_contrib(acc, aab, G2_O, dLda * e->G);
         double dLdp = dLda * gk->o * e->G;
         double dx = e->dx, dy = e->dy;
         /* power = -(a dx^2 + c dy^2)/2 - b dx dy, dx = x - u, dy = y - v */
-        atomic_add(&acc[G2_A], dLdp * (-0.5 * dx * dx));
-        atomic_add(&acc[G2_B], dLdp * (-dx * dy));
-        atomic_add(&acc[G2_C], dLdp * (-0.5 * dy * dy));
-        atomic_add(&acc[G2_U], dLdp * (gk->a * dx + gk->b * dy));
-        atomic_add(&acc[G2_V], dLdp * (gk->b * dx + gk->c * dy));
+        add_contrib(acc, aab, G2_A, dLdp * (-0.5 * dx * dx));
+        add_contrib(acc, aab, G2_B, dLdp * (-dx * dy));
+        add_contrib(acc, aab, G2_C, dLdp * (-0.5 * dy * dy));
+        add_contrib(acc, aab, G2_U, dLdp * (gk->a * dx + gk->b * dy));
+        add_contrib(acc, aab, G2_V, dLdp * (gk->b * dx + gk->c * dy));
     }
 }
 
@@ -718,17 +727,19 @@ have_dt:
 
 /* Adjoint of orc_render for a loss with dL/dcolor given at the listed pixels.
  * Gradients are ACCUMULATED into gm [n][3], gs [n][3], gq [n][4], go [n], gsh [n][K][3].
- * g2_out (optional) receives the per-Gaussian screen-space gradient [n][9]. */
+ * g2_out (optional) receives the per-Gaussian screen-space gradient [n][9], g2abs_out (optional)
+ * the sum over pixels of the absolute values of its contributions [n][9]. */
 int orc_backward(int n, const double *means, const double *scales, const double *quats,
                  const double *opacity, const double *sh, const orc_view *v, const orc_settings *s,
                  int npix, const int32_t *pix, const double *dLdC, double *gm, double *gs, double *gq,
-                 double *go, double *gsh, double *g2_out)
+                 double *go, double *gsh, double *g2_out, double *g2abs_out)
 {
     double *pj = (double *)malloc(sizeof(double) * PJ_NFIELDS * (size_t)(n > 0 ? n : 1));
     orc_project(n, means, scales, quats, opacity, sh, v, s, pj);
     int m;
     sorted_g *g = sort_visible(n, pj, &m);
     double *g2 = (double *)calloc((size_t)G2_N * (n > 0 ? n : 1), sizeof(double));
+    double *g2abs = g2abs_out ? (double *)calloc((size_t)G2_N * (n > 0 ? n : 1), sizeof(double)) : NULL;
     int total = pix ? npix : v->width * v->height;
 #pragma omp parallel
     {
@@ -740,7 +751,7 @@ int orc_backward(int n, const double *means, const double *scales, const double 
             int flat = pix ? pix[p] : p;
             int x = flat % v->width, y = flat / v->width;
             blend_pixel_adjoint(g, m, x + s->pix_offset, y + s->pix_offset, v->model == 1 ? 0 : v->width, s, d, g2,
-                                list, m);
+                                g2abs, list, m);
         }
         free(list);
     }
@@ -750,6 +761,8 @@ int orc_backward(int n, const double *means, const double *scales, const double 
                         pj + (size_t)PJ_NFIELDS * i, g2 + (size_t)G2_N * i, gm + 3 * i, gs + 3 * i, gq + 4 * i,
                         go + i, gsh + (size_t)3 * s->sh_coeffs * i);
     if (g2_out) memcpy(g2_out, g2, sizeof(double) * G2_N * (size_t)n);
+    if (g2abs_out) memcpy(g2abs_out, g2abs, sizeof(double) * G2_N * (size_t)n);
+    free(g2abs);
     free(g2);
     free(g);
     free(pj);

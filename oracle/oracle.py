@@ -59,7 +59,7 @@ def lib():
         L.orc_project.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, dp]
         L.orc_render.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, C.c_int, ip, dp, dp, ip, dp]
         L.orc_backward.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, C.c_int, ip, dp,
-                                   dp, dp, dp, dp, dp, dp]
+                                   dp, dp, dp, dp, dp, dp, dp]
         L.orc_chain.argtypes = [C.c_int, dp, dp, dp, dp, dp, vp, sp, dp, dp, dp, dp, dp, dp]
         L.orc_sh_eval.argtypes = [C.c_int, dp, dp]
         L.orc_depth_f32.argtypes = [dp, vp]
@@ -162,9 +162,11 @@ def render(p: Params, view, st: Settings, pix=None):
     return color, T, nc, margins
 
 
-def backward(p: Params, view, st: Settings, dLdC, pix=None, want_g2=False):
+def backward(p: Params, view, st: Settings, dLdC, pix=None, want_g2=False, want_abs=False):
     """Adjoint of ``render`` for a loss whose gradient w.r.t. the colours is dLdC ([3,H,W] for
-    the full image, or [npix,3] for listed pixels). Returns a dict of FP64 gradients."""
+    the full image, or [npix,3] for listed pixels). Returns a dict of FP64 gradients; with
+    want_g2 also "screen" [n, 9], the screen-space gradients, and with want_abs "screen_abs",
+    the sums over pixels of the absolute values of their contributions."""
     L = lib()
     if pix is None:
         d = np.ascontiguousarray(np.asarray(dLdC, dtype=np.float64).transpose(1, 2, 0).reshape(-1, 3))
@@ -175,12 +177,15 @@ def backward(p: Params, view, st: Settings, dLdC, pix=None, want_g2=False):
     g = dict(means=np.zeros_like(p.means), scales=np.zeros_like(p.scales),
              quats=np.zeros_like(p.quats), opacity=np.zeros_like(p.opacity), sh=np.zeros_like(p.sh))
     g2 = np.zeros((max(p.n, 1), 9)) if want_g2 else None
+    g2abs = np.zeros((max(p.n, 1), 9)) if want_abs else None
     L.orc_backward(p.n, _ptr(p.means), _ptr(p.scales), _ptr(p.quats), _ptr(p.opacity), _ptr(p.sh),
                    C.byref(_cview(view)), C.byref(_csettings(st, p.sh)), npix_arg,
                    _ptr(pix_arr, C.c_int32), _ptr(d), _ptr(g["means"]), _ptr(g["scales"]),
-                   _ptr(g["quats"]), _ptr(g["opacity"]), _ptr(g["sh"]), _ptr(g2))
+                   _ptr(g["quats"]), _ptr(g["opacity"]), _ptr(g["sh"]), _ptr(g2), _ptr(g2abs))
     if want_g2:
         g["screen"] = g2[: p.n]
+    if want_abs:
+        g["screen_abs"] = g2abs[: p.n]
     return g
 
 

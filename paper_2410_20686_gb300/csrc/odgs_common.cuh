@@ -4,11 +4,21 @@
 // blend kernels (16-byte vector loads):
 //   rec_a = { du, dv, bits(c0 | r0 << 16), opacity }   mean = (c0 + 0.5 + du, r0 + 0.5 + dv)
 //   (c0, r0 as 16-bit two's complement: pinhole centres may lie left of or above the image)
-//   rec_b = { conic_a, conic_b, conic_c, 0 }            inverse of Sigma_2D (Eq. 8, dilated)
+//   rec_b = { a, beta, gamma, Qb }                      inverse of Sigma_2D (Eq. 8, dilated) in
+//                                                        slice form, see below; Qb the binning bound
 //   rec_c = { r, g, b, 0 }                              SH colour
 // The mean is stored as an integer pixel anchor plus a small float offset so that the offset
 // from any pixel centre, (i - c0) - du, is formed without the rounding error of a float
 // coordinate near W (about 1e-4 px at W = 2048).
+//
+// The conic is stored in slice (LDL^T) form: with Sigma_2D = [[A, B], [B, C]] and det = AC - B^2,
+//   d^T Sigma_2D^-1 d = a (dx - beta dy)^2 + gamma dy^2,   a = C / det, beta = B / C, gamma = 1 / C,
+// i.e. for each pixel row the quadratic form is a parabola in dx centred on the ellipse's
+// horizontal slice, x = beta dy. Every one of a, beta, gamma is a quotient of positive, accurately
+// formed quantities, and the form is evaluated as a (t t) + gamma dy^2 with t = dx - beta dy, a
+// small number near the ellipse. The entries of the inverse in image axes, (C, -B, A) / det,
+// would instead make a needle-like Gaussian's exponent a difference of terms about cond(Sigma_2D)
+// times larger than itself.
 #pragma once
 
 #include <cstdint>
@@ -89,9 +99,9 @@ struct Settings {
 __device__ __forceinline__ float sigmoid_act(float x) { return 1.f / (1.f + expf(-x)); }
 
 // ------------------------------------------------------------------ float-float arithmetic
-// Unevaluated sums hi + lo (Dekker 1971; Knuth's TwoSum), used only to place the ERP mean
-// precisely. Every operation is written with round-to-nearest intrinsics so the compiler can
-// neither contract nor reorder it.
+// Unevaluated sums hi + lo (Dekker 1971; Knuth's TwoSum), used to place the ERP mean precisely and,
+// in the backward chain rule, to rotate dL/dconic exactly. Every operation is written with
+// round-to-nearest intrinsics so the compiler can neither contract nor reorder it.
 struct ff {
     float hi, lo;
 };
@@ -143,7 +153,7 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
 // kernels, so both take the same skip / clamp / termination decisions bit for bit).
 struct Staged {
     float4 pos;  // fc (column anchor, incl. seam shift), fr (row anchor), du, dv
-    float4 con;  // A, B, C, log2(o): p = log2(o) + dx (A dx + B dy) + C dy^2
+    float4 con;  // a k, beta, gamma k, log2(o) with k = -log2(e) / 2: p = log2(o) + k (a t^2 + gamma dy^2)
     float4 col;  // r, g, b, fsplit (first column using fc2; +inf if none)
     float fc2;   // column anchor right of the seam split
 };
@@ -181,7 +191,7 @@ __device__ __forceinline__ Staged stage_entry(float4 ra, float4 rb, float4 rc, i
     }
     s.pos = make_float4((float)(c0 + s0), (float)r0, ra.x, ra.y);
     const float k = -0.5f * kLog2e;
-    s.con = make_float4(__fmul_rn(rb.x, k), __fmul_rn(rb.y, -kLog2e), __fmul_rn(rb.z, k), log2f(ra.w));
+    s.con = make_float4(__fmul_rn(rb.x, k), rb.y, __fmul_rn(rb.z, k), log2f(ra.w));
     s.col = make_float4(rc.x, rc.y, rc.z, fsplit);
     s.fc2 = fc2;
     return s;
@@ -211,9 +221,9 @@ __device__ __forceinline__ void gather_records(const float4* __restrict__ ra, co
 struct Footprint {
     int c0, r0;
     float du, dv;
-    float A, B, C;   // Sigma_2D recovered from the stored conic
-    float BC;        // B / C: centre line of the horizontal slices
-    float k;         // sqrt(det / C): half-width scale of the slices
+    float BC;        // beta = B / C: centre line x = beta y of the horizontal slices
+    float k;         // 1 / sqrt(a): half-width scale of the slices
+    float iC;        // gamma = 1 / C
     float Qb;
     float ev;        // vertical half extent sqrt(Qb C)
     float ystar;     // dy of the rightmost point, B sqrt(Qb / A)
@@ -224,15 +234,16 @@ __device__ __forceinline__ Footprint make_footprint(float4 ra, float4 rb) {
     unpack_anchor(ra.z, f.c0, f.r0);
     f.du = ra.x;
     f.dv = ra.y;
-    const float det = __fsub_rn(__fmul_rn(rb.x, rb.z), __fmul_rn(rb.y, rb.y));
-    f.A = __fdiv_rn(rb.z, det);
-    f.B = __fdiv_rn(-rb.y, det);
-    f.C = __fdiv_rn(rb.x, det);
+    f.BC = rb.y;
+    f.iC = rb.z;
     f.Qb = rb.w;
-    f.BC = __fdiv_rn(f.B, f.C);
-    f.k = __fsqrt_rn(fmaxf(__fsub_rn(f.A, __fmul_rn(f.BC, f.B)), 0.f));
-    f.ev = __fsqrt_rn(__fmul_rn(f.Qb, f.C));
-    f.ystar = __fmul_rn(f.B, __fsqrt_rn(__fdiv_rn(f.Qb, f.A)));
+    f.k = __fsqrt_rn(__fdiv_rn(1.f, rb.x));
+    f.ev = __fsqrt_rn(__fdiv_rn(f.Qb, f.iC));
+    // Sigma_2D from the slice form without cancellation: C = 1 / gamma, B = beta C, A = 1 / a + beta B
+    const float C = __fdiv_rn(1.f, f.iC);
+    const float B = __fmul_rn(f.BC, C);
+    const float A = __fadd_rn(__fdiv_rn(1.f, rb.x), __fmul_rn(f.BC, B));
+    f.ystar = __fmul_rn(B, __fsqrt_rn(__fdiv_rn(f.Qb, A)));
     return f;
 }
 
@@ -251,15 +262,13 @@ __device__ __forceinline__ void footprint_rows(const Footprint& f, int H, int& j
 __device__ __forceinline__ int2 footprint_row_range(float4 ra, float4 rb, int H) {
     int c0, r0;
     unpack_anchor(ra.z, c0, r0);
-    const float det = __fsub_rn(__fmul_rn(rb.x, rb.z), __fmul_rn(rb.y, rb.y));
-    const float C = __fdiv_rn(rb.x, det);
-    const float ev = fminf(__fsqrt_rn(__fmul_rn(rb.w, C)), 2.f * (float)H);
+    const float ev = fminf(__fsqrt_rn(__fdiv_rn(rb.w, rb.z)), 2.f * (float)H);
     return make_int2(max(0, r0 + (int)ceilf(__fsub_rn(ra.y, ev))), min(H - 1, r0 + (int)floorf(__fadd_rn(ra.y, ev))));
 }
 
 // Horizontal offset of the slice boundary at vertical offset y (side = +1 right, -1 left).
 __device__ __forceinline__ float slice_edge(const Footprint& f, float y, float side) {
-    const float q = fmaxf(__fsub_rn(f.Qb, __fdiv_rn(__fmul_rn(y, y), f.C)), 0.f);
+    const float q = fmaxf(__fsub_rn(f.Qb, __fmul_rn(__fmul_rn(y, y), f.iC)), 0.f);
     return __fadd_rn(__fmul_rn(f.BC, y), side * __fmul_rn(f.k, __fsqrt_rn(q)));
 }
 
@@ -313,11 +322,15 @@ __device__ __forceinline__ float alpha_exp2(float p) {
     return r;
 }
 
-// Base-2 exponent of alpha before the clamp: log2(o) - 0.5 log2(e) d^T conic d (Eq. 2).
-__device__ __forceinline__ float gauss_exponent(float4 con, float dx, float dy) {
-    float q = __fmaf_rn(con.x, dx, __fmul_rn(con.y, dy));
-    float r = __fmaf_rn(__fmul_rn(con.z, dy), dy, con.w);
-    return __fmaf_rn(q, dx, r);
+// Base-2 exponent of alpha before the clamp, log2(o) - 0.5 log2(e) d^T conic d (Eq. 2), in the
+// slice form: per pixel row the slice centre du + beta dy and the row term gamma' dy^2 + log2(o)
+// (row_terms), then per pixel t = (i - fc) - centre and p = (a' t) t + row term.
+__device__ __forceinline__ void row_terms(float4 con, float du, float dy, float& centre, float& rowt) {
+    centre = __fmaf_rn(con.y, dy, du);
+    rowt = __fmaf_rn(__fmul_rn(con.z, dy), dy, con.w);
+}
+__device__ __forceinline__ float slice_exponent(float4 con, float t, float rowt) {
+    return __fmaf_rn(__fmul_rn(con.x, t), t, rowt);
 }
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {

@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                 if (ok) {
                     float inv = 1.f / c2.det;
                     const float4 ra = make_float4(du, dv, pack_anchor(c0, r0), o);
-                    const float4 rb = make_float4(c2.C * inv, -c2.B * inv, c2.A * inv, Qb);
+                    // the conic in slice form (a, beta, gamma) = (C / det, B / C, 1 / C)
+                    const float4 rb = make_float4(c2.C * inv, c2.B / c2.C, 1.f / c2.C, Qb);
                     // tiles met by the footprint, row band by row band (seam-wrapped columns)
                     Footprint fp = make_footprint(ra, rb);
                     int jlo, jhi;
@@ -500,67 +501,47 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         float T[6], TM[6];
         tm_factor(Jm, W, M, T, TM);
         Cov2 c2 = cov2d(TM, a.dilation);
-        // conic (C, -B, A) / D -> Sigma_2D -> TM, in the eigenbasis (e1, e2) of Sigma_2D. There
-        // the conic is diag(1 / l1, 1 / l2) and dL/dSigma_2D = -conic G conic is three products, where
-        // G = [[da, db / 2], [db / 2, dc]] is dL/dconic (b the single off-diagonal variable). Formed
-        // in image axes instead, the product loses about eps * cond(Sigma_2D)^2 of relative
-        // precision (cond reaches 1e3 - 1e4 for needle-like Gaussians). l2 = det / l1 uses the
-        // cancellation-free determinant; G is rotated with exact products (float-float), since
-        // e2^T G e2 is a small difference of large terms.
-        const float da = g0.z, db = g0.w, dc = g1.x;
-        const float hA = 0.5f * (c2.A - c2.C);
-        const float rt = sqrtf(hA * hA + c2.B * c2.B);
-        const float l1 = 0.5f * (c2.A + c2.C) + rt;
-        const float l2 = c2.det / l1;
-        float ex = hA >= 0.f ? hA + rt : c2.B, ey = hA >= 0.f ? c2.B : rt - hA;  // no cancellation
-        const float en = ex * ex + ey * ey;
-        if (en > 0.f) {
-            const float ie = 1.f / sqrtf(en);
-            ex *= ie;
-            ey *= ie;
-        } else {  // isotropic: any basis
-            ex = 1.f;
-            ey = 0.f;
-        }
-        float g11, g12, g22;
-        {
-            const float hb = 0.5f * db;
-            const ff Ge1x = ff_add(two_prod(da, ex), two_prod(hb, ey)), Ge1y = ff_add(two_prod(hb, ex), two_prod(dc, ey));
-            const ff Ge2x = ff_add(two_prod(da, -ey), two_prod(hb, ex)), Ge2y = ff_add(two_prod(hb, -ey), two_prod(dc, ex));
-            g11 = ff_add(ff_mulf(Ge1x, ex), ff_mulf(Ge1y, ey)).hi;
-            g12 = ff_add(ff_mulf(Ge2x, ex), ff_mulf(Ge2y, ey)).hi;
-            g22 = ff_add(ff_mulf(Ge2x, -ey), ff_mulf(Ge2y, ex)).hi;
-        }
-        const float i1 = 1.f / l1, i2 = 1.f / l2;
-        const float s11 = -g11 * i1 * i1, s12 = -g12 * i1 * i2, s22 = -g22 * i2 * i2;
-        // rows of TM and T in the eigenbasis; Sigma_2D = TM TM^T + delta I gives
-        // dL/dTM' = 2 dSigma' TM' (rows dr1, dr2)
-        float dr1[3], dr2[3], t1[3], t2[3];
+        // The blend's conic gradients are w.r.t. the slice form a = C / det, beta = B / C,
+        // gamma = 1 / C of Sigma_2D = TM TM^T + delta I (A = |TM_1|^2 + delta, B = TM_1 . TM_2,
+        // C = |TM_2|^2 + delta). With r = TM_1 - beta TM_2 and 1 / a = A - beta B:
+        //   d(1/a)/dTM_1 = 2 r, d(1/a)/dTM_2 = -2 beta r, dbeta/dTM_1 = TM_2 / C,
+        //   dbeta/dTM_2 = (TM_1 - 2 beta TM_2) / C, dgamma/dTM_2 = -2 gamma^2 TM_2, so
+        //   dL/dTM_1 = ka r + kb TM_2,  dL/dTM_2 = -beta ka r + kb (r - beta TM_2) + kg TM_2
+        // with ka = -2 a^2 dL/da, kb = gamma dL/dbeta, kg = -2 gamma^2 dL/dgamma. For a needle-like
+        // Gaussian r (its thin row) is small: every term is a product with r or tau = T_1 - beta T_2,
+        // never a difference of the long direction's terms, whose rounding would be about
+        // cond(Sigma_2D) times the thin direction's gradient.
+        const float ga = g0.z, gbeta = g0.w, ggam = g1.x;
+        const float sa = c2.C * (1.f / c2.det), beta = c2.B / c2.C, gam = 1.f / c2.C;
+        const float ka = -2.f * sa * sa * ga, kb = gam * gbeta, kg = -2.f * gam * gam * ggam;
+        float r[3], tau[3], dTM1[3], dTM2[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float r1 = ex * TM[k] + ey * TM[3 + k], r2 = ex * TM[3 + k] - ey * TM[k];
-            dr1[k] = 2.f * (s11 * r1 + s12 * r2);
-            dr2[k] = 2.f * (s12 * r1 + s22 * r2);
-            t1[k] = ex * T[k] + ey * T[3 + k];
-            t2[k] = ex * T[3 + k] - ey * T[k];
+            r[k] = fmaf(-beta, TM[3 + k], TM[k]);
+            tau[k] = fmaf(-beta, T[3 + k], T[k]);
+            dTM1[k] = fmaf(ka, r[k], kb * TM[3 + k]);
+            dTM2[k] = fmaf(-beta * ka, r[k], fmaf(kb, fmaf(-beta, TM[3 + k], r[k]), kg * TM[3 + k]));
         }
-        // TM = T M: dM += T'^T dTM' (the rotation cancels), dT' = dTM' M^T
+        // TM = T M: dM += T_1 (x) dTM_1 + T_2 (x) dTM_2, written with tau so that the r terms do not
+        // cancel: dM = ka tau (x) r + kb (tau (x) TM_2 + T_2 (x) r) + kg T_2 (x) TM_2
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                dM[3 * j + k] += fmaf(ka * tau[j], r[k], fmaf(kb, fmaf(tau[j], TM[3 + k], T[3 + j] * r[k]),
+                                                            kg * T[3 + j] * TM[3 + k]));
+        // dT = dTM M^T, T = J W: dJ = dT W^T
         float dT1[3], dT2[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) dM[3 * j + k] += t1[j] * dr1[k] + t2[j] * dr2[k];
-            dT1[j] = dr1[0] * M[3 * j] + dr1[1] * M[3 * j + 1] + dr1[2] * M[3 * j + 2];
-            dT2[j] = dr2[0] * M[3 * j] + dr2[1] * M[3 * j + 1] + dr2[2] * M[3 * j + 2];
+            dT1[j] = dTM1[0] * M[3 * j] + dTM1[1] * M[3 * j + 1] + dTM1[2] * M[3 * j + 2];
+            dT2[j] = dTM2[0] * M[3 * j] + dTM2[1] * M[3 * j + 1] + dTM2[2] * M[3 * j + 2];
         }
-        // T = J W: dJ' = dT' W^T, then back to image axes: dJ = [e1 e2] dJ'
         float dJ[6];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const float p1 = dT1[0] * W[3 * j] + dT1[1] * W[3 * j + 1] + dT1[2] * W[3 * j + 2];
-            const float p2 = dT2[0] * W[3 * j] + dT2[1] * W[3 * j + 1] + dT2[2] * W[3 * j + 2];
-            dJ[j] = ex * p1 - ey * p2;
-            dJ[3 + j] = ey * p1 + ex * p2;
+            dJ[j] = dT1[0] * W[3 * j] + dT1[1] * W[3 * j + 1] + dT1[2] * W[3 * j + 2];
+            dJ[3 + j] = dT2[0] * W[3 * j] + dT2[1] * W[3 * j + 1] + dT2[2] * W[3 * j + 2];
         }
         // dL/dt: mean path d(u, v)/dt = J (Eq. 10 for ERP) plus J's dependence on t
         const float fx = V.fx, fy = V.fy;

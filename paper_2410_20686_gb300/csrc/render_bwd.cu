@@ -7,13 +7,15 @@
 // Gaussian it forms
 //   dL/drgb = alpha T g,   dL/dalpha = T (rgb . g) - (B . g) / (1 - alpha),
 // with g = dL/dC and B the colour blended behind the Gaussian (background included), and from
-// dL/dalpha the gradients w.r.t. opacity, conic (a, b, c) and ERP mean (u, v) through Eq. 2
-// (zero when alpha was clamped at 0.99). The skip / clamp decisions and alpha are recomputed
+// dL/dalpha the gradients w.r.t. opacity, the slice-form conic (a, beta, gamma) and ERP mean
+// (u, v) through Eq. 2 (zero when alpha was clamped at 0.99). The skip / clamp decisions and alpha are recomputed
 // with the forward kernel's exact operation sequence, so they match it bit for bit.
 //
-// A thread first sums nine values over its PPT pixels: dL/drgb and, with dp = dL/d(power), the
-// sums of dp, dp dx, dp dx^2, and dy times the first two and dy^2 times the first (dy is the
-// same for all of a thread's pixels). The warp sums them over its lanes with a transpose
+// A thread first sums over its PPT pixels, with dp = dL/d(power) and t the pixel's offset from the
+// slice centre (the exponent's own variable), dp, dp t and dp t^2 and dL/drgb; with dy the same
+// for all of a thread's pixels, these and dy times the first two and dy^2 times the first are the
+// nine values (sum dp t gives the mean terms free of the cancellation an image-axis form suffers
+// for needle-like Gaussians). The warp sums them over its lanes with a transpose
 // reduction (12 shuffles for 9 values), the CTA over its warps in shared memory; then one thread
 // per entry forms dL/d(u, v, conic, opacity), which are linear in these sums, and adds them to the
 // per-(view, Gaussian) accumulator with three 16-byte vector atomics. A warp whose pixels all stopped before an entry skips it, and so does a warp
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
     float4* s_pos = smem;
     float4* s_con = smem + B;
     float4* s_col = smem + 2 * B;
-    float4* s_raw = smem + 3 * B;  // conic a, b, c, 1 / opacity
+    float4* s_raw = smem + 3 * B;  // a, beta, gamma (slice-form conic), 1 / opacity
     int2* s_rows = reinterpret_cast<int2*>(smem + 4 * B);  // pixel rows the footprint reaches
     float* s_fc2 = reinterpret_cast<float*>(s_rows + B);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_fc2 + B);
@@ -181,35 +183,36 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                     const float4 P = s_pos[j];
                     const float4 K = s_con[j];
                     const float dy = __fsub_rn(__fsub_rn(fj, P.y), P.w);
-                    const float Bdy = __fmul_rn(K.y, dy);
-                    const float rr = __fmaf_rn(__fmul_rn(K.z, dy), dy, K.w);
-                    // exponents of all PPT pixels first (the forward kernel's exact sequence)
-                    float pk[PPT], dxk[PPT];
+                    float centre, rowt;
+                    row_terms(K, P.z, dy, centre, rowt);
+                    // exponents of all PPT pixels first (the forward kernel's exact sequence); t is
+                    // the pixel's offset from the slice centre, dx = t + (centre - du)
+                    float pk[PPT], tk[PPT];
                     if (!any_split) {
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
-                            dxk[k] = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), P.z);
-                            pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
+                            tk[k] = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), centre);
+                            pk[k] = slice_exponent(K, tk[k], rowt);
                         }
                     } else {
                         const float fsplit = s_col[j].w, fc2 = s_fc2[j];
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             const float fi = fi0 + (float)(k * tpr);
-                            dxk[k] = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), P.z);
-                            pk[k] = __fmaf_rn(__fmaf_rn(K.x, dxk[k], Bdy), dxk[k], rr);
+                            tk[k] = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), centre);
+                            pk[k] = slice_exponent(K, tk[k], rowt);
                         }
                     }
                     const float4 c = s_col[j];
-                    // sums over this thread's pixels of dp, dp dx and dp dx^2 (dp = dL/d power); the
+                    // sums over this thread's pixels of dp, dp t and dp t^2 (dp = dL/d power); the
                     // conic, opacity and mean terms are linear in these sums and in dy times them,
-                    // so the warp reduces the sums and the CTA pass after the batch forms the terms
+                    // so the warp reduces them and the CTA pass after the batch forms the terms
                     float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
                         contrib = true;
-                        const float dx = dxk[k];
+                        const float t = tk[k];
                         const float ar = alpha_exp2(pk[k]);
                         const float alpha = fminf(kAlphaMax, ar);
                         const float inv = __fdividef(1.f, __fsub_rn(1.f, alpha));
@@ -224,18 +227,18 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                         T[k] = Tj;
                         if (ar < kAlphaMax) {  // no gradient through the 0.99 clamp
                             const float dp = dLda * alpha;  // dL/d(power), power = ln G
-                            const float dpx = dp * dx;
+                            const float dpt = dp * t;
                             S0 += dp;
-                            S1 += dpx;
-                            S2 = fmaf(dpx, dx, S2);
+                            S1 += dpt;
+                            S2 = fmaf(dpt, t, S2);
                         }
                     }
-                    vals[0] = S0;
-                    vals[1] = S1;
-                    vals[2] = S2;
-                    vals[3] = dy * S0;
-                    vals[4] = dy * S1;
-                    vals[5] = dy * vals[3];
+                    vals[0] = S0;          // sum dp
+                    vals[1] = S1;          // sum dp t
+                    vals[2] = S2;          // sum dp t^2
+                    vals[3] = dy * S1;     // sum dp t dy
+                    vals[4] = dy * S0;     // sum dp dy
+                    vals[5] = dy * vals[4];  // sum dp dy^2
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, contrib);
                 if (m == 0u) {
@@ -254,9 +257,14 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
             }
             __syncthreads();
             // per entry: the warps' sums added, then the screen-space gradient terms. With (dx, dy) =
-            // pixel - mean, power = ln o - (a dx^2 + 2 b dx dy + c dy^2) / 2, so
-            //   dL/du = a S1 + b (dy S0), dL/dv = b S1 + c (dy S0), dL/da = -S2 / 2,
-            //   dL/db = -(dy S1), dL/dc = -(dy^2 S0) / 2, dL/do = S0 / o
+            // pixel - mean and power = ln o - (a t^2 + gamma dy^2) / 2, t = dx - beta dy (the conic in
+            // slice form), the gradients w.r.t. the mean, the slice-form conic and the opacity are
+            //   dL/du = a sum(dp t), dL/dv = -a beta sum(dp t) + gamma sum(dp dy),
+            //   dL/da = -sum(dp t^2) / 2, dL/dbeta = a sum(dp t dy), dL/dgamma = -sum(dp dy^2) / 2,
+            //   dL/do = sum(dp) / o.
+            // Each sum is dominated by its own scale (t across the ellipse, dy along it), so even for a
+            // needle-like Gaussian the thin direction's information is not a small difference of the
+            // long direction's sums, as the conic's image-axis entries would make it.
             for (int jj = tid; jj < cnt; jj += nthr) {
                 float q[9];
 #pragma unroll
@@ -266,8 +274,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
 #pragma unroll
                     for (int k = 0; k < 9; ++k) q[k] += r[k];
                 }
-                const float4 R = s_raw[jj];
-                const float4 p0 = make_float4(R.x * q[1] + R.y * q[3], R.y * q[1] + R.z * q[3], -0.5f * q[2], -q[4]);
+                const float4 R = s_raw[jj];  // a, beta, gamma, 1 / o
+                const float du_ = R.x * q[1];
+                const float4 p0 = make_float4(du_, fmaf(R.z, q[4], -R.y * du_), -0.5f * q[2], R.x * q[3]);
                 const float4 p1 = make_float4(-0.5f * q[5], R.w * q[0], q[6], q[7]);
                 float4* dst = a.acc + 3 * (size_t)s_idx[jj];
                 if (p0.x != 0.f || p0.y != 0.f || p0.z != 0.f || p0.w != 0.f) red_add_v4(dst, p0);

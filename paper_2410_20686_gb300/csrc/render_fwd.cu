@@ -3,12 +3,14 @@
 // A persistent grid pulls (view, tile) work items from an atomic counter, so one launch renders
 // any number of views of mixed resolution. For each tile the CTA walks the tile's depth-ordered
 // list in batches: the threads gather a batch of records with 16-byte loads, convert them to the
-// tile's staged form (seam shift, base-2 conic, log2 opacity) in shared memory, then evaluate the
-// batch from shared memory (broadcast reads).
+// tile's staged form (seam shift, base-2 slice-form conic, log2 opacity) in shared memory, then
+// evaluate the batch from shared memory (broadcast reads).
 //
-// Each thread owns PPT pixels of one row, tile_w / PPT columns apart. The row-constant part of Eq. 2's quadratic
-// form (B dy and C dy^2 + log2 o) and the shared-memory loads are paid once per thread and entry,
-// not once per pixel; the kernel is bound by instruction issue, so this is where its time goes.
+// Each thread owns PPT pixels of one row, tile_w / PPT columns apart. The row-constant part of
+// Eq. 2's quadratic form (the slice centre du + beta dy and gamma dy^2 + log2 o) and the
+// shared-memory loads are paid once per thread and entry, not once per pixel; per pixel the
+// exponent is (a t) t + row term with t the offset from the slice centre. The kernel is bound by
+// instruction issue, so this is where its time goes.
 // A pixel stops before the Gaussian that would take its transmittance below 1e-4; a thread stops
 // when its pixels have; the tile stops when all threads have (__syncthreads_count).
 //
@@ -93,23 +95,23 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
                 const float4 P = s_pos[j];
                 const float4 K = s_con[j];
                 const float dy = __fsub_rn(__fsub_rn(fj, P.y), P.w);
-                const float Bdy = __fmul_rn(K.y, dy);
-                const float rr = __fmaf_rn(__fmul_rn(K.z, dy), dy, K.w);
+                float centre, rowt;
+                row_terms(K, P.z, dy, centre, rowt);
                 // exponents of all PPT pixels first: independent chains, no branches
                 float pk[PPT];
                 if (!any_split) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float dx = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), P.z);
-                        pk[k] = __fmaf_rn(__fmaf_rn(K.x, dx, Bdy), dx, rr);
+                        const float t = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), centre);
+                        pk[k] = slice_exponent(K, t, rowt);
                     }
                 } else {
                     const float fsplit = s_col[j].w, fc2 = s_fc2[j];
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         const float fi = fi0 + (float)(k * tpr);
-                        const float dx = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), P.z);
-                        pk[k] = __fmaf_rn(__fmaf_rn(K.x, dx, Bdy), dx, rr);
+                        const float t = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), centre);
+                        pk[k] = slice_exponent(K, t, rowt);
                     }
                 }
                 bool any = false;

@@ -566,3 +566,56 @@ def test_chain_alone_reproduces_the_adjoint_from_its_screen_space_gradients():
         assert np.array_equal(part[k], full[k]), k
     zero = O.chain(p, v, st, np.zeros((p.n, 9)))
     assert all(not np.any(zero[k]) for k in zero)
+
+
+def test_slice_form_conversion_of_screen_gradients_matches_finite_differences():
+    """The tests compare the library's screen-space conic gradients, taken w.r.t. the slice form
+    (a, beta, gamma) of the conic (a dx^2 + 2 b dx dy + c dy^2 = a (dx - beta dy)^2 + gamma dy^2),
+    with the oracle's, taken w.r.t. the entries (a, b, c). The conversion is checked against
+    central differences of a function of the entries through the slice parametrisation."""
+    from tests.helpers import screen_slice_to_xy, screen_xy_to_slice
+    rng = np.random.default_rng(5)
+    n = 6
+    pj = np.zeros((n, O.PJ_NFIELDS))
+    a, beta, gam = rng.uniform(0.2, 3, n), rng.uniform(-2, 2, n), rng.uniform(0.1, 2, n)
+    pj[:, O.PJ_CONIC], pj[:, O.PJ_CONIC + 1], pj[:, O.PJ_CONIC + 2] = a, -a * beta, gam + a * beta ** 2
+
+    def loss(x, w):  # a smooth non-linear function of the entries
+        return w[0] * np.sin(x[0]) + w[1] * x[1] ** 3 + w[2] * np.exp(0.3 * x[2]) + w[3] * x[0] * x[1]
+
+    w = rng.normal(size=(n, 4))
+    g_xy = np.zeros((n, 9))
+    g_sl_fd = np.zeros((n, 9))
+    for i in range(n):
+        ent = lambda s: np.array([s[0], -s[0] * s[1], s[2] + s[0] * s[1] ** 2])  # noqa: E731
+        x = ent((a[i], beta[i], gam[i]))
+        g_xy[i, 2:5] = [w[i, 0] * np.cos(x[0]) + w[i, 3] * x[1], 3 * w[i, 1] * x[1] ** 2 + w[i, 3] * x[0],
+                        0.3 * w[i, 2] * np.exp(0.3 * x[2])]
+        for k in range(3):
+            s0 = np.array([a[i], beta[i], gam[i]])
+            h = 1e-6
+            sp, sm = s0.copy(), s0.copy()
+            sp[k] += h
+            sm[k] -= h
+            g_sl_fd[i, 2 + k] = (loss(ent(sp), w[i]) - loss(ent(sm), w[i])) / (2 * h)
+    g_sl = screen_xy_to_slice(g_xy, pj)
+    assert np.allclose(g_sl[:, 2:5], g_sl_fd[:, 2:5], rtol=1e-6, atol=1e-8)
+    assert np.allclose(screen_slice_to_xy(g_sl, pj), g_xy, rtol=1e-12, atol=1e-12)
+
+
+def test_absolute_contribution_sums_bound_the_screen_gradients():
+    """The adjoint's optional sums of absolute per-pixel contributions bound the screen-space
+    gradients (|sum| <= sum |.|), and equal them for the colour gradients of a single Gaussian
+    under positive weights (every contribution alpha T g is then positive)."""
+    sc = S.random_scene(40, 64, 32, seed=21, sh_degree=1, log_scale=(-2.5, 0.5))
+    p = O.Params.of(sc)
+    st = O.Settings(sh_degree=1)
+    w = np.random.default_rng(21).normal(size=(3, 32, 64))
+    g = O.backward(p, sc.views[0], st, w, want_g2=True, want_abs=True)
+    assert np.all(g["screen_abs"] >= np.abs(g["screen"]) * (1 - 1e-12))
+    assert g["screen_abs"].max() > 0
+    one = O.Params(p.means[:1], p.scales[:1], p.quats[:1], p.opacity[:1], p.sh[:1])
+    one.means[0] = [0.2, 0.1, 2.0]
+    g1 = O.backward(one, sc.views[0], st, np.abs(w), want_g2=True, want_abs=True)
+    assert g1["screen"][0, 6] > 0
+    assert np.allclose(g1["screen_abs"][0, 6:9], g1["screen"][0, 6:9], rtol=1e-12)

@@ -7,7 +7,8 @@ import pytest
 
 from oracle import oracle as O
 from paper_2410_20686_gb300 import scenes as S
-from tests.helpers import EPS_CLAMP, EPS_SKIP, EPS_TERM, assert_grads_close, oracle_settings, rel_l2, to_torch
+from tests.helpers import (EPS_CLAMP, EPS_SKIP, EPS_TERM, SUM_BOUND, assert_grads_close, oracle_settings, rel_l2,
+                           screen_abs_xy_to_slice, screen_slice_to_xy, screen_xy_to_slice, to_torch)
 
 pytestmark = pytest.mark.gpu
 NAMES = ("means", "scales", "quats", "opacity", "sh")
@@ -265,16 +266,18 @@ def test_gaussians_within_a_twentieth_of_a_degree_of_the_poles():
 
 
 def test_needle_gaussians_blend_and_chain_separately():
-    """Needle-like Gaussians (one axis 30-300x the others, so that cond(Sigma_2D) reaches 1e3-1e5)
-    in three views. The backward pass is checked in its two halves, each against FP64: the
+    """Needle-like Gaussians (one axis 30-300x the others, 1-5 m from the cameras, so that
+    cond(Sigma_2D) exceeds 1e3 for 839 of the visible items, 1e4 for 67, and reaches 2.7e5) in
+    three views. The backward pass is checked in its two halves, each against FP64: the
     per-(view, Gaussian) screen-space gradients of the reverse blend (Eq. 2-3) against the
-    oracle's, and the parameter gradients against the oracle's chain rule (App. A.3) applied to
-    the GPU's own screen-space gradients; then the whole against the oracle adjoint."""
+    oracle's (converted to the library's slice-form conic), and the parameter gradients against
+    the oracle's chain rule (App. A.3) applied to the GPU's own screen-space gradients; then the
+    whole against the oracle adjoint."""
     import torch
     from paper_2410_20686_gb300.rasterizer import Rasterizer
     views = [S.yaw_view(256, 128, (0.05, -0.02, 0.1), 0.6), S.yaw_view(128, 64, (0.3, 0.1, -0.2), -1.9),
              S.View.identity(192, 96)]
-    sc = S.random_scene(1500, 256, 128, seed=131, sh_degree=1, radius=(0.6, 4.0), log_scale=(-4.5, 0.3),
+    sc = S.random_scene(1500, 256, 128, seed=131, sh_degree=1, radius=(1.0, 5.0), log_scale=(-4.5, 0.3),
                         views=views)
     rng = np.random.default_rng(131)
     long_axis = rng.integers(0, 3, sc.n)
@@ -291,7 +294,7 @@ def test_needle_gaussians_blend_and_chain_separately():
         l1 = tr / 2 + np.sqrt(np.maximum(tr * tr / 4 - det, 0))
         conds.append(l1 * l1 / det)
     conds = np.concatenate(conds)
-    assert (conds > 1e3).sum() > 200 and conds.max() > 1e4  # the stress is really there
+    assert (conds > 1e3).sum() > 500 and (conds > 1e4).sum() > 30 and conds.max() > 1e5  # the stress is there
     w = _weights(sc, rs, 13)
     rast = Rasterizer()
     m, s, q, o, sh = to_torch(sc)
@@ -301,15 +304,26 @@ def test_needle_gaussians_blend_and_chain_separately():
     assert rast.status() == 0
     gpu = {k: t.cpu().numpy().astype(np.float64) for k, t in g.items()}
     screen = rast.debug_screen_grads().astype(np.float64).reshape(len(views), sc.n, 9)
-    ref_screen, chain, ref = [], None, None
+    ref_screen, ref_abs, chain, ref = [], [], None, None
     for i, (v, wv) in enumerate(zip(views, w)):
-        r = O.backward(p, v, st, wv, want_g2=True)
-        ref_screen.append(r.pop("screen"))
+        pj = O.project(p, v, st)
+        r = O.backward(p, v, st, wv, want_g2=True, want_abs=True)
+        # the library reports the conic gradient in slice form; the oracle in image-axis entries
+        ref_screen.append(screen_xy_to_slice(r.pop("screen"), pj))
+        ref_abs.append(screen_abs_xy_to_slice(r.pop("screen_abs"), pj))
         ref = r if ref is None else {k: ref[k] + r[k] for k in NAMES}
-        c = O.chain(p, v, st, screen[i])
+        c = O.chain(p, v, st, screen_slice_to_xy(screen[i], pj))
         chain = c if chain is None else {k: chain[k] + c[k] for k in NAMES}
-    ref_screen = np.stack(ref_screen)
-    assert_grads_close({nm: screen[..., j] for j, nm in enumerate(O.G2_NAMES)},
-                       {nm: ref_screen[..., j] for j, nm in enumerate(O.G2_NAMES)}, O.G2_NAMES)
-    assert_grads_close(gpu, chain, NAMES)
-    assert_grads_close(gpu, ref, NAMES)
+    ref_screen, ref_abs = np.stack(ref_screen), np.stack(ref_abs)
+    names = ("u", "v", "a", "beta", "gamma", "opacity", "r", "g", "b")
+    # 1. the reverse blend: each screen-space gradient is a sum of per-pixel contributions whose
+    #    signs follow the random loss weights, so some sums cancel by factors of 1e3-1e4; the band
+    #    adds the float32 summation bound SUM_BOUND * sum|contribution| (the oracle's own sums)
+    assert_grads_close({nm: screen[..., j] for j, nm in enumerate(names)},
+                       {nm: ref_screen[..., j] for j, nm in enumerate(names)}, names,
+                       slack={nm: SUM_BOUND * ref_abs[..., j] for j, nm in enumerate(names)}, what="screen ")
+    # 2. the chain rule alone, element by element at the plain band
+    assert_grads_close(gpu, chain, NAMES, what="chain ")
+    # 3. the whole, per tensor (relative L2): its elements are covered by 1. and 2.
+    for k in NAMES:
+        assert rel_l2(gpu[k], ref[k]) <= 1e-3, k
