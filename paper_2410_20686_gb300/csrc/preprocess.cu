@@ -218,11 +218,21 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int stride
 
 // ------------------------------------------------------------------ forward projection
 
-__global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// Footprints with at most this many row bands are counted by their own thread; larger ones (the
+// pole-stretched Gaussians) by the whole warp, one band per lane.
+constexpr int kThreadBands = 4;
+static_assert(kThreadBands <= 6, "the per-thread loop stores the spans of six bands (rect, rect2)");
+
+__global__ void __launch_bounds__(256, 3) k_preprocess_geom(PreArgs a) {
+    const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     unsigned long long local_pairs = 0ull;
     uint32_t local_visible = 0u;
-    if (g < a.n) {
+    // every lane of a warp runs the view loop (lanes past the end as culled items), so that the
+    // warp can count the tiles of many-band footprints together
+    const bool act = g0 < a.n;
+    const int g = act ? g0 : 0;
+    {
         const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
         float s0 = __ldg(a.scales + 3 * g), s1 = __ldg(a.scales + 3 * g + 1), s2 = __ldg(a.scales + 3 * g + 2);
         const float4 q = __ldg(reinterpret_cast<const float4*>(a.quats) + g);
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                         isfinite(s2) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && isfinite(o);
             const float* shg = a.sh + (size_t)g * 3 * a.sh_coeffs;
             for (int k = 0; k < 3 * a.sh_coeffs; ++k) finite_in = finite_in && isfinite(__ldg(shg + k));
-            if (!finite_in) atomicOr(&a.hdr->status, kStNonfinite);
+            if (act && !finite_in) atomicOr(&a.hdr->status, kStNonfinite);
         }
 
         // Sigma = M M^T with M = R(q) S (Sec. 3.1)
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
             uint4 rect = make_uint4(0u, 0u, 0u, 0u);
             uint32_t key = 0xFFFFFFFFu;
             const float r = depth_key(V, m0, m1, m2);
-            bool ok = finite_in && (r > a.st.r_near) && (r < a.st.r_far) && (Qalpha > 0.f);
+            bool ok = act && finite_in && (r > a.st.r_near) && (r < a.st.r_far) && (Qalpha > 0.f);
             // camera-space mean in float-float: t = W mu + t_wc
             ff t[3];
 #pragma unroll
@@ -310,59 +320,108 @@ __global__ void __launch_bounds__(256) k_preprocess_geom(PreArgs a) {
                 ff be = ff_add(ff_mul(rho, cth), ff_mul(ny, sth));          // r cos(theta - theta0)
                 dv = -atan2f(ae.hi, be.hi) * V.fy;
             }
+            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+            Footprint fp{};
+            int jlo = 0, jhi = -1;
             if (ok) {
                 // Sigma_2D = (J W M)(J W M)^T + delta I  (Eq. 8 and Sec. 3.1)
                 float T[6], TM[6];
                 tm_factor(J, V.R, M, T, TM);
                 Cov2 c2 = cov2d(TM, a.st.dilation);
-                ok = c2.det > 0.f;
-                if (ok) {
+                if (c2.det > 0.f) {
                     float inv = 1.f / c2.det;
-                    const float4 ra = make_float4(du, dv, pack_anchor(c0, r0), o);
+                    ra = make_float4(du, dv, pack_anchor(c0, r0), o);
                     // the conic in slice form (a, beta, gamma) = (C / det, B / C, 1 / C)
-                    const float4 rb = make_float4(c2.C * inv, c2.B / c2.C, 1.f / c2.C, Qb);
-                    // tiles met by the footprint, row band by row band (seam-wrapped columns)
-                    Footprint fp = make_footprint(ra, rb);
-                    int jlo, jhi;
+                    rb = make_float4(c2.C * inv, c2.B / c2.C, 1.f / c2.C, Qb);
+                    fp = make_footprint(ra, rb);
                     footprint_rows(fp, V.H, jlo, jhi);
-                    uint32_t count = 0u, sp0 = 0u, sp1 = 0u, sp2 = 0u, sp3 = 0u, sp4 = 0u, sp5 = 0u;
-                    const int th = a.st.tile_h;
-                    const int ty0 = jlo / th, ty1 = jhi / th;
-                    if (jlo <= jhi) {
-                        for (int ty = ty0; ty <= ty1; ++ty) {
-                            int st0, cnt;
-                            band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.st.tile_w,
-                                         V.tiles_x, V.model == 0, st0, cnt);
-                            count += (uint32_t)cnt;
-                            // spans of the first six bands (scalars, so that they stay in registers)
-                            const uint32_t sp = (uint32_t)st0 | ((uint32_t)cnt << 16);
-                            const int b = ty - ty0;
-                            sp0 = b == 0 ? sp : sp0; sp1 = b == 1 ? sp : sp1; sp2 = b == 2 ? sp : sp2;
-                            sp3 = b == 3 ? sp : sp3; sp4 = b == 4 ? sp : sp4; sp5 = b == 5 ? sp : sp5;
-                        }
-                    }
-                    if (count > 0u) {
-                        rect = make_uint4((uint32_t)ty0 | ((uint32_t)(ty1 - ty0 + 1) << 16), count, sp0, sp1);
-                        if (ty1 - ty0 >= 2) a.rect2[item] = make_uint4(sp2, sp3, sp4, sp5);
-                        local_pairs += count;
-                        ++local_visible;
-                        key = __float_as_uint(r);
-                        a.rec_a[item] = ra;
-                        a.rec_b[item] = rb;
-                    }
                 }
             }
-            if (key == 0xFFFFFFFFu) {
-                // culled: finite records that never pass the alpha test (opacity 0), so that an
-                // index that reaches the blend only through a sort that gave up reads no stale
-                // memory (the colour kernel writes rec_c of the visible items only)
-                a.rec_a[item] = make_float4(0.f, 0.f, 0.f, 0.f);
-                a.rec_b[item] = make_float4(1.f, 0.f, 1.f, 0.f);
-                a.rec_c[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // tiles met by the footprint, row band by row band (seam-wrapped columns)
+            const bool cand = jlo <= jhi;
+            const int th = a.st.tile_h;
+            const int ty0 = cand ? jlo / th : 0, nb = cand ? jhi / th - ty0 + 1 : 0;
+            uint32_t count = 0u, sp0 = 0u, sp1 = 0u, sp2 = 0u, sp3 = 0u, sp4 = 0u, sp5 = 0u;
+            if (nb <= kThreadBands) {
+                for (int b = 0; b < nb; ++b) {
+                    const int ty = ty0 + b;
+                    int st0, cnt;
+                    band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.st.tile_w, V.tiles_x,
+                                 V.model == 0, st0, cnt);
+                    count += (uint32_t)cnt;
+                    // spans of the first bands (scalars, so that they stay in registers)
+                    const uint32_t sp = (uint32_t)st0 | ((uint32_t)cnt << 16);
+                    sp0 = b == 0 ? sp : sp0; sp1 = b == 1 ? sp : sp1; sp2 = b == 2 ? sp : sp2;
+                    sp3 = b == 3 ? sp : sp3; sp4 = b == 4 ? sp : sp4; sp5 = b == 5 ? sp : sp5;
+                }
             }
-            a.rect[item] = rect;
-            a.dkey[item] = key;
-            a.dval[item] = (uint32_t)item;
+            // footprints of many row bands (pole-stretched Gaussians cover up to all rows): the
+            // warp counts each one's bands together, one band per lane, with the same band_columns
+            // on the same floats, so that counts and spans are the per-thread loop's, bit for bit
+            unsigned many = __ballot_sync(0xffffffffu, nb > kThreadBands);
+            while (many) {
+                const int src = __ffs(many) - 1;
+                many &= many - 1u;
+                Footprint f;
+                f.c0 = __shfl_sync(0xffffffffu, fp.c0, src);
+                f.r0 = __shfl_sync(0xffffffffu, fp.r0, src);
+                f.du = __shfl_sync(0xffffffffu, fp.du, src);
+                f.dv = __shfl_sync(0xffffffffu, fp.dv, src);
+                f.BC = __shfl_sync(0xffffffffu, fp.BC, src);
+                f.k = __shfl_sync(0xffffffffu, fp.k, src);
+                f.iC = __shfl_sync(0xffffffffu, fp.iC, src);
+                f.Qb = __shfl_sync(0xffffffffu, fp.Qb, src);
+                f.ev = __shfl_sync(0xffffffffu, fp.ev, src);
+                f.ystar = __shfl_sync(0xffffffffu, fp.ystar, src);
+                const int wjlo = __shfl_sync(0xffffffffu, jlo, src), wjhi = __shfl_sync(0xffffffffu, jhi, src);
+                const int wty0 = __shfl_sync(0xffffffffu, ty0, src), wnb = __shfl_sync(0xffffffffu, nb, src);
+                uint32_t tot = 0u, w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u, w4 = 0u, w5 = 0u;
+                for (int b0 = 0; b0 < wnb; b0 += 32) {
+                    const int b = b0 + lane;
+                    int st0 = 0, cnt = 0;
+                    if (b < wnb) {
+                        const int ty = wty0 + b;
+                        band_columns(f, max(wjlo, ty * th), min(wjhi, ty * th + th - 1), V.W, a.st.tile_w,
+                                     V.tiles_x, V.model == 0, st0, cnt);
+                    }
+                    uint32_t c = (uint32_t)cnt;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+                    tot += c;
+                    if (b0 == 0) {
+                        const uint32_t sp = (uint32_t)st0 | ((uint32_t)cnt << 16);
+                        w0 = __shfl_sync(0xffffffffu, sp, 0); w1 = __shfl_sync(0xffffffffu, sp, 1);
+                        w2 = __shfl_sync(0xffffffffu, sp, 2); w3 = __shfl_sync(0xffffffffu, sp, 3);
+                        w4 = __shfl_sync(0xffffffffu, sp, 4); w5 = __shfl_sync(0xffffffffu, sp, 5);
+                    }
+                }
+                if (lane == src) {
+                    count = tot;
+                    sp0 = w0; sp1 = w1; sp2 = w2; sp3 = w3; sp4 = w4; sp5 = w5;
+                }
+            }
+            if (count > 0u) {
+                rect = make_uint4((uint32_t)ty0 | ((uint32_t)nb << 16), count, sp0, sp1);
+                if (nb > 2) a.rect2[item] = make_uint4(sp2, sp3, sp4, sp5);
+                local_pairs += count;
+                ++local_visible;
+                key = __float_as_uint(r);
+                a.rec_a[item] = ra;
+                a.rec_b[item] = rb;
+            }
+            if (act) {
+                if (key == 0xFFFFFFFFu) {
+                    // culled: finite records that never pass the alpha test (opacity 0), so that an
+                    // index that reaches the blend only through a sort that gave up reads no stale
+                    // memory (the colour kernel writes rec_c of the visible items only)
+                    a.rec_a[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    a.rec_b[item] = make_float4(1.f, 0.f, 1.f, 0.f);
+                    a.rec_c[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                a.rect[item] = rect;
+                a.dkey[item] = key;
+                a.dval[item] = (uint32_t)item;
+            }
         }
     }
     // frame pair and visible-item counts
