@@ -231,7 +231,8 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     Header* hdr = reinterpret_cast<Header*>(w + c->L.hdr);
     ViewDev* vd = reinterpret_cast<ViewDev*>(w + c->L.views);
     float4* trig = reinterpret_cast<float4*>(w + c->L.trig);
-    if (launch_setup(c->tab, vd, trig, hdr, c->geo.total_trig, st) != cudaSuccess) return ODGS_ERR_CUDA;
+    uint32_t* dhist = reinterpret_cast<uint32_t*>(w + c->L.sort_hist);
+    if (launch_setup(c->tab, vd, trig, hdr, c->geo.total_trig, dhist, st) != cudaSuccess) return ODGS_ERR_CUDA;
     c->launches += 1;
     PreArgs a{};
     a.means = c->g.means; a.scales = c->g.scales; a.quats = c->g.quats; a.opacity = c->g.opacity; a.sh = c->g.sh;
@@ -250,6 +251,7 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.rect2 = reinterpret_cast<uint4*>(w + c->L.rect2);
     a.dkey = reinterpret_cast<uint32_t*>(w + c->L.dkey0);
     a.dval = reinterpret_cast<uint32_t*>(w + c->L.dval0);
+    a.dhist = dhist;
     a.hdr = hdr;
     if (launch_preprocess(a, c->s.sh_degree, st) != cudaSuccess) return ODGS_ERR_CUDA;
     if (c->n > 0) c->launches += 2;
@@ -323,13 +325,13 @@ odgs_status odgs_get_status(odgs_ctx* c, uint32_t* bits, void* stream) {
 static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     uint8_t* w = c->ws;
     Header* hdr = reinterpret_cast<Header*>(w + c->L.hdr);
-    // 1. depth sort of all (view, Gaussian) items
+    // 1. depth sort of all (view, Gaussian) items (digit histograms counted by the preprocess)
     uint32_t* dk[2] = {reinterpret_cast<uint32_t*>(w + c->L.dkey0), reinterpret_cast<uint32_t*>(w + c->L.dkey1)};
     uint32_t* dv[2] = {reinterpret_cast<uint32_t*>(w + c->L.dval0), reinterpret_cast<uint32_t*>(w + c->L.dval1)};
     int rb = 0;
     if (launch_radix_sort(dk, dv, &hdr->n_items, c->geo.n_items, 32, reinterpret_cast<uint32_t*>(w + c->L.sort_hist),
                           reinterpret_cast<uint32_t*>(w + c->L.sort_ctr), reinterpret_cast<uint32_t*>(w + c->L.sort_lb),
-                          &hdr->status, c->num_sms, st, &rb, &c->launches, /*hist_ready=*/false,
+                          &hdr->status, c->num_sms, st, &rb, &c->launches, /*hist_ready=*/true,
                           c->wait_limit) != cudaSuccess)
         return ODGS_ERR_CUDA;
     c->depth_buf = rb;

@@ -63,6 +63,7 @@ struct PreArgs {
     uint4* rect;   // (ty0 | bands << 16, tiles, span of band 0, span of band 1); span = start | count << 16
     uint4* rect2;  // spans of bands 2..5 (items with more than 2 bands)
     uint32_t *dkey, *dval;
+    uint32_t* dhist;  // [4][256] digit histograms of dkey (zeroed by k_setup), for the depth sort
     Header* hdr;
 };
 
@@ -149,7 +150,7 @@ struct BwdArgs {
 };
 
 cudaError_t launch_setup(const ViewTable& tab, ViewDev* views, float4* trig, Header* hdr, int total_trig,
-                         cudaStream_t st);
+                         uint32_t* dhist, cudaStream_t st);
 cudaError_t launch_preprocess(const PreArgs& a, int sh_degree, cudaStream_t st);
 cudaError_t launch_preprocess_bwd(const PreBwdArgs& a, int sh_degree, cudaStream_t st);
 

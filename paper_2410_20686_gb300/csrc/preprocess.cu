@@ -1,7 +1,7 @@
 // Per-Gaussian kernels of the ODGS ERP rasterizer (sm_103a):
 //   k_setup                per-view tables (pixel-centre cos/sin in float-float), header reset
 //   k_preprocess_geom      forward projection per (Gaussian, view): Sec. 3.1-3.2, Eq. 4-8
-//   k_preprocess_color     SH colour per visible (Gaussian, view)
+//   k_preprocess_color     SH colour per visible (Gaussian, view); digit histograms of the depth keys
 //   k_preprocess_bwd       chain rule from screen-space gradients to the parameters: App. A.3
 // The forward's geometry and colour halves are separate kernels so that the geometry does not
 // carry the 48 SH coefficients in registers. The backward stays one kernel: split, it would read
@@ -15,9 +15,11 @@ namespace odgs {
 
 // ------------------------------------------------------------------ setup
 
-__global__ void k_setup(ViewTable tab, ViewDev* views, float4* trig, Header* hdr, int total_trig) {
+__global__ void k_setup(ViewTable tab, ViewDev* views, float4* trig, Header* hdr, int total_trig, uint32_t* dhist) {
     int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid < tab.n_views) views[gid] = tab.v[gid];
+    // the depth sort's digit histograms, counted by k_preprocess_geom
+    for (int i = gid; i < 4 * 256; i += gridDim.x * blockDim.x) dhist[i] = 0u;
     if (gid == 0) {
         hdr->pairs = 0ull;
         hdr->pairs_emitted = 0ull;
@@ -453,7 +455,22 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_geom(PreArgs a) {
 template <int DEG>
 __global__ void __launch_bounds__(256) k_preprocess_color(PreArgs a) {
     constexpr int K = (DEG + 1) * (DEG + 1);
+    // digit histograms of the depth keys for the depth sort (all items, culled ones included),
+    // counted here, where every key is read anyway and the kernel waits on memory
+    __shared__ uint32_t s_dh[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_dh[i >> 8][i & 255] = 0u;
+    __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int v = 0; v < a.n_views && g < a.n; ++v) {
+        const uint32_t key = a.dkey[(size_t)v * a.n + g];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_dh[p][(key >> (8 * p)) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        const uint32_t c = s_dh[i >> 8][i & 255];
+        if (c) atomicAdd(a.dhist + i, c);
+    }
     if (g >= a.n) return;
     const float m0 = __ldg(a.means + 3 * g), m1 = __ldg(a.means + 3 * g + 1), m2 = __ldg(a.means + 3 * g + 2);
     bool loaded = false;
@@ -769,11 +786,11 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
 // ------------------------------------------------------------------ launchers
 
 cudaError_t launch_setup(const ViewTable& tab, ViewDev* views, float4* trig, Header* hdr, int total_trig,
-                         cudaStream_t st) {
+                         uint32_t* dhist, cudaStream_t st) {
     int threads = 256;
     int blocks = (max(total_trig, tab.n_views) + threads - 1) / threads;
     blocks = max(1, min(blocks, 1024));
-    k_setup<<<blocks, threads, 0, st>>>(tab, views, trig, hdr, total_trig);
+    k_setup<<<blocks, threads, 0, st>>>(tab, views, trig, hdr, total_trig, dhist);
     return cudaGetLastError();
 }
 

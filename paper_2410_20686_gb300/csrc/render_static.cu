@@ -125,7 +125,7 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
 
     // ---- the forward path (same kernels as the workspace entry points)
     int launches = 0;
-    if (launch_setup(tab, vd, trig, hdr, geo.total_trig, strm) != cudaSuccess) return ODGS_ERR_CUDA;
+    if (launch_setup(tab, vd, trig, hdr, geo.total_trig, d_hist, strm) != cudaSuccess) return ODGS_ERR_CUDA;
     PreArgs a{};
     a.means = g->means; a.scales = g->scales; a.quats = g->quats; a.opacity = g->opacity; a.sh = g->sh;
     a.n = g->n; a.n_views = 1; a.sh_coeffs = st.sh_coeffs;
@@ -137,11 +137,12 @@ extern "C" odgs_status odgs_render_fwd_static(const odgs_gaussians* g, const odg
     a.st.raw = st.raw_params;
     a.st.checked = st.checked;
     a.rec_a = rec_a; a.rec_b = rec_b; a.rec_c = rec_c; a.rect = rect; a.rect2 = rect2; a.dkey = dk[0]; a.dval = dv[0];
+    a.dhist = d_hist;
     a.hdr = hdr;
     if (launch_preprocess(a, st.sh_degree, strm) != cudaSuccess) return ODGS_ERR_CUDA;
     int rb = 0;
     if (launch_radix_sort(dk, dv, &hdr->n_items, n, 32, d_hist, d_ctr, d_lb, &hdr->status, num_sms, strm, &rb,
-                          &launches, /*hist_ready=*/false, kDefaultWaitLimit) != cudaSuccess)
+                          &launches, /*hist_ready=*/true, kDefaultWaitLimit) != cudaSuccess)
         return ODGS_ERR_CUDA;
     BinArgs b{};
     b.sorted_idx = dv[rb]; b.rect = rect; b.rect2 = rect2; b.views = vd; b.n_per_view = g->n > 0 ? g->n : 1;
