@@ -109,7 +109,10 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
         const int x0 = tx * tw;
         const int xp = x0 + lx0, y = ty * a.tile_h + ly;
         const bool inside = y < V.H;
-        const float fi0 = (float)xp, fj = (float)y;
+        const float fj = (float)y;
+        float fik[PPT];  // column coordinates of the thread's pixels
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) fik[k] = (float)(xp + k * tpr);
         const uint2 rg = a.ranges[item];
         // entries past the tile's range (possible only when the lists were rebuilt after a sort
         // that gave up, so that they differ from the forward's) stage as never-blending entries
@@ -175,14 +178,15 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                     if (lane < 9) red[lane] = 0.f;
                     continue;
                 }
-                float vals[9];
-#pragma unroll
-                for (int q = 0; q < 9; ++q) vals[q] = 0.f;
+                // sums over this thread's pixels of dp, dp t and dp t^2 (dp = dL/d power) and of
+                // dL/drgb; the conic, opacity and mean terms are linear in these and in dy times them,
+                // so the warp reduces them and the CTA pass after the batch forms the terms
+                float S0 = 0.f, S1 = 0.f, S2 = 0.f, V0 = 0.f, V1 = 0.f, V2 = 0.f, dy = 0.f;
                 bool contrib = false;
                 if (e < tmax) {
                     const float4 P = s_pos[j];
                     const float4 K = s_con[j];
-                    const float dy = __fsub_rn(__fsub_rn(fj, P.y), P.w);
+                    dy = __fsub_rn(__fsub_rn(fj, P.y), P.w);
                     float centre, rowt;
                     row_terms(K, P.z, dy, centre, rowt);
                     // exponents of all PPT pixels first (the forward kernel's exact sequence); t is
@@ -191,23 +195,18 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                     if (!any_split) {
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
-                            tk[k] = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), centre);
+                            tk[k] = __fsub_rn(__fsub_rn(fik[k], P.x), centre);
                             pk[k] = slice_exponent(K, tk[k], rowt);
                         }
                     } else {
                         const float fsplit = s_col[j].w, fc2 = s_fc2[j];
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
-                            const float fi = fi0 + (float)(k * tpr);
-                            tk[k] = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), centre);
+                            tk[k] = __fsub_rn(__fsub_rn(fik[k], (fik[k] >= fsplit) ? fc2 : P.x), centre);
                             pk[k] = slice_exponent(K, tk[k], rowt);
                         }
                     }
                     const float4 c = s_col[j];
-                    // sums over this thread's pixels of dp, dp t and dp t^2 (dp = dL/d power); the
-                    // conic, opacity and mean terms are linear in these sums and in dy times them,
-                    // so the warp reduces them and the CTA pass after the batch forms the terms
-                    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (e >= nl[k] || pk[k] < kLog2AlphaMin) continue;
@@ -219,9 +218,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                         const float Tj = T[k] * inv;
                         const float w = alpha * Tj;
                         const float cg = c.x * g0[k] + c.y * g1[k] + c.z * g2[k];
-                        vals[6] += w * g0[k];
-                        vals[7] += w * g1[k];
-                        vals[8] += w * g2[k];
+                        V0 = fmaf(w, g0[k], V0);
+                        V1 = fmaf(w, g1[k], V1);
+                        V2 = fmaf(w, g2[k], V2);
                         const float dLda = Tj * cg - Bg[k] * inv;
                         Bg[k] = fmaf(cg, w, Bg[k]);
                         T[k] = Tj;
@@ -233,17 +232,16 @@ __global__ void __launch_bounds__(256) k_render_bwd(BwdArgs a) {
                             S2 = fmaf(dpt, t, S2);
                         }
                     }
-                    vals[0] = S0;          // sum dp
-                    vals[1] = S1;          // sum dp t
-                    vals[2] = S2;          // sum dp t^2
-                    vals[3] = dy * S1;     // sum dp t dy
-                    vals[4] = dy * S0;     // sum dp dy
-                    vals[5] = dy * vals[4];  // sum dp dy^2
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, contrib);
                 if (m == 0u) {
                     if (lane < 9) red[lane] = 0.f;
-                } else if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction needed
+                    continue;
+                }
+                // sum dp, sum dp t, sum dp t^2, sum dp t dy, sum dp dy, sum dp dy^2, dL/drgb
+                const float dyS0 = dy * S0;
+                const float vals[9] = {S0, S1, S2, dy * S1, dyS0, dy * dyS0, V0, V1, V2};
+                if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction needed
                     if (contrib) {
 #pragma unroll
                         for (int q = 0; q < 9; ++q) red[q] = vals[q];

@@ -62,7 +62,10 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
         const int x0 = tx * tw;
         const int xp = x0 + lx0, y = ty * a.tile_h + ly;
         const bool inside = y < V.H;
-        const float fi0 = (float)xp, fj = (float)y;
+        const float fj = (float)y;
+        float fik[PPT];  // column coordinates of the thread's pixels
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) fik[k] = (float)(xp + k * tpr);
         const uint2 rg = a.ranges[item];
         const int n = (int)(rg.y - rg.x);
 
@@ -102,15 +105,14 @@ __global__ void __launch_bounds__(256) k_render_fwd(FwdArgs a) {
                 if (!any_split) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float t = __fsub_rn(__fsub_rn(fi0 + (float)(k * tpr), P.x), centre);
+                        const float t = __fsub_rn(__fsub_rn(fik[k], P.x), centre);
                         pk[k] = slice_exponent(K, t, rowt);
                     }
                 } else {
                     const float fsplit = s_col[j].w, fc2 = s_fc2[j];
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float fi = fi0 + (float)(k * tpr);
-                        const float t = __fsub_rn(__fsub_rn(fi, (fi >= fsplit) ? fc2 : P.x), centre);
+                        const float t = __fsub_rn(__fsub_rn(fik[k], (fik[k] >= fsplit) ? fc2 : P.x), centre);
                         pk[k] = slice_exponent(K, t, rowt);
                     }
                 }
