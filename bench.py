@@ -208,8 +208,8 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
 # bench reports null until it is captured again.
 PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh"),
                     "structs": ("odgs_internal.h", "BwdArgs"),
-                    "sha256": "6dbdcdde91622ad219c79f8fc23ce82453e9fa758de767749c0052f4cb5c961d",
-                    "bytes": 170656256}
+                    "sha256": "75b2371e9f5110aa2072aafd59988b09542bf9ee94fb3b9a1de6a42539162aea",
+                    "bytes": 171217408}
 
 
 def kernel_sources_digest(spec=PROFILED_TRAFFIC):
