@@ -498,7 +498,11 @@ __global__ void __launch_bounds__(256) k_preprocess_color(PreArgs a) {
 
 // ------------------------------------------------------------------ backward chain rule
 
-template <int DEG>
+// ONE: a frame of one view. Its colour phase reads the SH coefficient row twice (colours, then
+// the direction's gradient) and forms dL/dsh = m_c dL/drgb_c Y_k when it writes them (m_c = 0 for
+// a clamped channel), so neither the 48 coefficients nor 48 accumulators stay in registers.
+// Frames of several views accumulate dL/dsh over the views in registers.
+template <int DEG, bool ONE>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -690,12 +694,81 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         gq[0] = (dw - qw * dot) / qn; gq[1] = (dx - qx * dot) / qn;
         gq[2] = (dy - qy * dot) / qn; gq[3] = (dz - qz * dot) / qn;
     }
-    // colour phase (after the geometry, so that its 96 SH registers are not live together with
-    // the covariance chain): dL/dsh and the view direction's gradient, view by view
-    float gsh[16][3];
+    // colour phase (after the geometry, so that its SH registers are not live together with the
+    // covariance chain): dL/dsh and the view direction's gradient, view by view
+    constexpr int KG = ONE ? 1 : 16;
+    float gsh[KG][3];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
-    if (any) {
+    for (int k = 0; k < KG; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+    float ysh[ONE ? 16 : 1], msh[3] = {0.f, 0.f, 0.f};  // one view: dL/dsh[k][c] = msh[c] ysh[k]
+#pragma unroll
+    for (int k = 0; k < (ONE ? 16 : 1); ++k) ysh[k] = 0.f;
+    if (ONE && any) {
+        const float4 g1 = a.acc[1 + 3 * (size_t)g], g2 = a.acc[2 + 3 * (size_t)g];
+        if (g1.z != 0.f || g1.w != 0.f || g2.x != 0.f) {
+            const ViewDev& V = a.views[0];
+            const float vx = m0 - V.cam[0], vy = m1 - V.cam[1], vz = m2 - V.cam[2];
+            const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+            const float x = vx * il, y = vy * il, z = vz * il;
+            float Y[16];
+            sh_basis<DEG>(x, y, z, Y);
+            const float drgb[3] = {g1.z, g1.w, g2.x};
+            const float* shg = a.sh + (size_t)g * a.sh_coeffs * 3;
+            // two passes over the coefficient row, 16-byte loads where the rows allow them (the
+            // second pass hits L1): the colours (which channels are clamped), then the weights
+            // w_k = sum over unclamped channels of dL/drgb_c sh_kc of the direction's gradient
+            const bool vec = (a.sh_coeffs * 3) % 4 == 0;
+            float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int i = 0; i < (K * 3 + 3) / 4; ++i) {
+                float q[4];
+                if (vec) {
+                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(shg) + i);
+                    q[0] = t4.x; q[1] = t4.y; q[2] = t4.z; q[3] = t4.w;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) q[r] = 4 * i + r < K * 3 ? __ldg(shg + 4 * i + r) : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int e = 4 * i + r;
+                    if (e < K * 3) col[e % 3] = fmaf(q[r], Y[e / 3], col[e % 3]);
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) msh[ch] = col[ch] < 0.f ? 0.f : drgb[ch];  // clamped channels
+            if (DEG > 0) {
+                float w[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) w[k] = 0.f;
+#pragma unroll
+                for (int i = 0; i < (K * 3 + 3) / 4; ++i) {
+                    float q[4];
+                    if (vec) {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(shg) + i);
+                        q[0] = t4.x; q[1] = t4.y; q[2] = t4.z; q[3] = t4.w;
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) q[r] = 4 * i + r < K * 3 ? __ldg(shg + 4 * i + r) : 0.f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int e = 4 * i + r;
+                        if (e < K * 3) w[e / 3] = fmaf(msh[e % 3], q[r], w[e / 3]);
+                    }
+                }
+                float gx, gy, gz;
+                sh_grad_acc<DEG>(x, y, z, w, gx, gy, gz);
+                const float dd = gx * x + gy * y + gz * z;  // project out the radial part
+                gm[0] += (gx - dd * x) * il;
+                gm[1] += (gy - dd * y) * il;
+                gm[2] += (gz - dd * z) * il;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) ysh[k] = Y[k];
+        }
+    }
+    if (!ONE && any) {
         float shc[16][3];
         load_sh<DEG>(a.sh, a.sh_coeffs, g, shc);
         for (int v = 0; v < a.n_views; ++v) {
@@ -720,7 +793,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
                 if (acc < 0.f) continue;  // clamped channel
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    gsh[k][ch] += drgb[ch] * Y[k];
+                    gsh[ONE ? 0 : k][ch] += drgb[ch] * Y[k];
                     wsum[k] += drgb[ch] * shc[k][ch];
                 }
             }
@@ -758,7 +831,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] += gsh[k][ch];
+            for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] += ONE ? msh[ch] * ysh[k] : gsh[ONE ? 0 : k][ch];
     } else {
 #pragma unroll
         for (int i = 0; i < 3; ++i) { pm[i] = gm[i]; ps[i] = gs[i]; }
@@ -769,14 +842,19 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
 #pragma unroll
             for (int i = 0; i < K * 3 / 4; ++i) {
                 const int e = 4 * i;
-                p4[i] = make_float4(gsh[e / 3][e % 3], gsh[(e + 1) / 3][(e + 1) % 3], gsh[(e + 2) / 3][(e + 2) % 3],
-                                    gsh[(e + 3) / 3][(e + 3) % 3]);
+                float q[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int kk = (e + r) / 3, ch = (e + r) % 3;
+                    q[r] = ONE ? msh[ch] * ysh[kk] : gsh[ONE ? 0 : kk][ch];
+                }
+                p4[i] = make_float4(q[0], q[1], q[2], q[3]);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] = gsh[k][ch];
+                for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] = ONE ? msh[ch] * ysh[k] : gsh[ONE ? 0 : k][ch];
         }
         for (int k = K; k < a.sh_coeffs; ++k)
             for (int ch = 0; ch < 3; ++ch) psh[3 * k + ch] = 0.f;
@@ -810,11 +888,16 @@ cudaError_t launch_preprocess(const PreArgs& a, int sh_degree, cudaStream_t st) 
 cudaError_t launch_preprocess_bwd(const PreBwdArgs& a, int sh_degree, cudaStream_t st) {
     if (a.n == 0) return cudaSuccess;
     int threads = 128, blocks = (a.n + threads - 1) / threads;
+    const bool one = a.n_views == 1;
     switch (sh_degree) {
-        case 0: k_preprocess_bwd<0><<<blocks, threads, 0, st>>>(a); break;
-        case 1: k_preprocess_bwd<1><<<blocks, threads, 0, st>>>(a); break;
-        case 2: k_preprocess_bwd<2><<<blocks, threads, 0, st>>>(a); break;
-        default: k_preprocess_bwd<3><<<blocks, threads, 0, st>>>(a); break;
+        case 0: one ? k_preprocess_bwd<0, true><<<blocks, threads, 0, st>>>(a)
+                    : k_preprocess_bwd<0, false><<<blocks, threads, 0, st>>>(a); break;
+        case 1: one ? k_preprocess_bwd<1, true><<<blocks, threads, 0, st>>>(a)
+                    : k_preprocess_bwd<1, false><<<blocks, threads, 0, st>>>(a); break;
+        case 2: one ? k_preprocess_bwd<2, true><<<blocks, threads, 0, st>>>(a)
+                    : k_preprocess_bwd<2, false><<<blocks, threads, 0, st>>>(a); break;
+        default: one ? k_preprocess_bwd<3, true><<<blocks, threads, 0, st>>>(a)
+                     : k_preprocess_bwd<3, false><<<blocks, threads, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }
