@@ -99,6 +99,23 @@ def test_recomputed_lists_give_the_same_gradients():
         assert rel_l2(b[k], a[k]) < 1e-6, k
 
 
+@pytest.mark.parametrize("tile_w,tile_h,ppt,ppt_bwd", [(16, 16, 2, 4), (32, 8, 1, 1), (32, 16, 2, 2), (8, 8, 1, 2),
+                                                     (16, 16, 4, 2)])
+def test_gradients_across_thread_layouts(tile_w, tile_h, ppt, ppt_bwd):
+    # Tile shapes and pixels per thread of both blend kernels (one to eight warps per tile in the
+    # backward pass; a forward thread's pixels spread over several backward threads in the last
+    # case): against the oracle, and against the same frame with its lists rebuilt for the
+    # backward pass (equal up to the order of the atomic sums).
+    sc = S.random_scene(900, 128, 64, seed=98, sh_degree=2, log_scale=(-2.6, 0.5))
+    kw = dict(sh_degree=2, tile_w=tile_w, tile_h=tile_h, pixels_per_thread=ppt, pixels_per_thread_bwd=ppt_bwd)
+    w = _weights(sc, _rs(**kw), 6)
+    a = _gpu_grads(sc, _rs(**kw), w)
+    b = _gpu_grads(sc, _rs(recompute_lists=True, **kw), w)
+    for k in NAMES:
+        assert rel_l2(b[k], a[k]) < 1e-6, k
+    _assert_close(a, _oracle_grads(sc, _rs(**kw), w))
+
+
 def test_autograd_function_matches_direct_backward():
     import torch
     from paper_2410_20686_gb300.rasterizer import render
