@@ -105,6 +105,15 @@ typedef struct {
                            for NaN / inf: an offending Gaussian is culled in every view, an
                            offending gradient value counts as 0, and ODGS_DEV_NONFINITE is set.
                            0: no checks (non-finite inputs give unspecified results)      */
+    int full_lists;     /* 0: odgs_bin_sort cuts each tile's list after the depth at which every
+                           pixel of the tile has provably stopped (T < 1e-4): it sums, depth
+                           bucket by depth bucket, -log2(1 - a) over the Gaussians whose alpha
+                           is at least a >= 1/255 at all the tile's pixel centres (the minimum
+                           of a convex exponent over the tile is at a corner pixel). Images,
+                           final T and gradients are the same as with the whole lists; fewer
+                           pairs are emitted and sorted. Frames of more than 2^19 tiles keep
+                           the whole lists. 1: the whole lists (every Gaussian whose footprint
+                           meets the tile)                                                 */
 } odgs_settings;
 
 /* Gaussian parameters, device pointers, float32, contiguous:

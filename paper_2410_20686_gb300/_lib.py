@@ -46,7 +46,7 @@ class Settings(C.Structure):
                 ("batch", C.c_int), ("cov_dilation", C.c_float), ("r_near", C.c_float), ("r_far", C.c_float),
                 ("bg", C.c_float * 3), ("recompute_lists", C.c_int), ("grad_accumulate", C.c_int),
                 ("pixels_per_thread", C.c_int), ("raw_params", C.c_int), ("pixels_per_thread_bwd", C.c_int),
-                ("checked", C.c_int)]
+                ("checked", C.c_int), ("full_lists", C.c_int)]
 
 
 class Gaussians(C.Structure):

@@ -18,7 +18,8 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t hdr, views, trig, rec_a, rec_b, rec_c, rect, rect2, dkey0, dkey1, dval0, dval1, block_sums, ranges, T_final,
-        n_last, acc, sort_hist, sort_ctr, sort_lb, big, total;
+        n_last, acc, sort_hist, sort_ctr, sort_lb, big, cover, cut, kcount, total;
+    bool truncate;  // the lists are truncated at saturated tiles (the tables below are present)
 };
 
 struct PairLayout {
@@ -26,8 +27,12 @@ struct PairLayout {
 };
 
 
-Layout make_layout(size_t items, const Geometry& g) {
+// Truncated lists unless the caller asks for the whole lists or the frame has too many tiles.
+bool truncates(const odgs_settings& s, const Geometry& g) { return !s.full_lists && (uint32_t)g.total_tiles <= kCutMaxTiles; }
+
+Layout make_layout(size_t items, const Geometry& g, bool truncate) {
     Layout L{};
+    L.truncate = truncate;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -55,6 +60,10 @@ Layout make_layout(size_t items, const Geometry& g) {
     L.sort_ctr = take(sizeof(uint32_t) * 4);
     L.sort_lb = take(sizeof(uint32_t) * radix_lookback_words(items));
     L.big = take(sizeof(uint2) * items);
+    const size_t tt = truncate ? (size_t)g.total_tiles : 0;
+    L.cover = take(sizeof(uint32_t) * (size_t)kCutBuckets * (truncate ? tt + 1 : 0));
+    L.cut = take(tt);
+    L.kcount = take(truncate ? sizeof(uint32_t) * items : 0);
     L.total = o;
     return L;
 }
@@ -101,6 +110,7 @@ odgs_status odgs::check_settings(const odgs_settings* s, odgs_settings* out) {
         if (!std::isfinite(t.bg[c])) return ODGS_ERR_INVALID_ARG;
     if (t.raw_params != 0 && t.raw_params != 1) return ODGS_ERR_INVALID_ARG;
     if (t.checked != 0 && t.checked != 1) return ODGS_ERR_INVALID_ARG;
+    if (t.full_lists != 0 && t.full_lists != 1) return ODGS_ERR_INVALID_ARG;
     *out = t;
     return ODGS_OK;
 }
@@ -174,6 +184,10 @@ struct odgs_ctx {
     int bwd_batch = 64;
     uint32_t wait_limit = kDefaultWaitLimit;
     int depth_buf = 0, pair_buf = 0;  // which buffer of each double-buffered sort holds its result
+    // the cut per tile and the kept counts per item of the current preprocess are in the
+    // workspace (they are computed from the depth keys by item, which the depth sort overwrites,
+    // so a second odgs_bin_sort or a rebuild of the lists reuses them)
+    bool cut_ready = false;
 };
 
 extern "C" {
@@ -216,7 +230,7 @@ odgs_status odgs_workspace_size(int n, const odgs_view* views, int n_views, cons
     Geometry g;
     r = build_geometry(views, n_views, st, n, &g, nullptr);
     if (r != ODGS_OK) return r;
-    *bytes = make_layout(g.n_items, g).total;
+    *bytes = make_layout(g.n_items, g, truncates(st, g)).total;
     return ODGS_OK;
 }
 
@@ -270,7 +284,7 @@ odgs_status odgs_preprocess(odgs_ctx* c, const odgs_gaussians* g, const odgs_vie
     Geometry geo;
     r = build_geometry(views, n_views, st, g->n, &geo, &tab);
     if (r != ODGS_OK) return r;
-    Layout L = make_layout(geo.n_items, geo);
+    Layout L = make_layout(geo.n_items, geo, truncates(st, geo));
     if (!workspace) return ODGS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0) return ODGS_ERR_INVALID_ARG;
     if (ws_bytes < L.total) return ODGS_ERR_WORKSPACE;
@@ -286,6 +300,7 @@ odgs_status odgs_preprocess(odgs_ctx* c, const odgs_gaussians* g, const odgs_vie
     c->ws_bytes = ws_bytes;
     c->stage = 0;
     c->launches = 0;
+    c->cut_ready = false;
     c->bwd_batch = std::min(st.batch, 64);
     const int bwd_threads = st.tile_w * st.tile_h / st.pixels_per_thread_bwd;
     while (c->bwd_batch > 8 && render_bwd_smem(c->bwd_batch, bwd_threads) > 48 * 1024) c->bwd_batch /= 2;
@@ -325,6 +340,27 @@ odgs_status odgs_get_status(odgs_ctx* c, uint32_t* bits, void* stream) {
 static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     uint8_t* w = c->ws;
     Header* hdr = reinterpret_cast<Header*>(w + c->L.hdr);
+    // 0. which tiles saturate, and from which depth on (before the depth sort reorders the keys)
+    if (c->L.truncate && !c->cut_ready) {
+        SatArgs sa{};
+        sa.rect = reinterpret_cast<const uint4*>(w + c->L.rect);
+        sa.rec_a = reinterpret_cast<const float4*>(w + c->L.rec_a);
+        sa.rec_b = reinterpret_cast<const float4*>(w + c->L.rec_b);
+        sa.dkey = reinterpret_cast<const uint32_t*>(w + c->L.dkey0);
+        sa.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
+        sa.n_per_view = c->n > 0 ? c->n : 1;
+        sa.n_items = (uint32_t)c->geo.n_items;
+        sa.total_tiles = (uint32_t)c->geo.total_tiles;
+        sa.tile_w = c->s.tile_w;
+        sa.tile_h = c->s.tile_h;
+        uint32_t rn;
+        std::memcpy(&rn, &c->s.r_near, sizeof(rn));
+        sa.base = rn >> kCutShift;
+        sa.cover = reinterpret_cast<uint32_t*>(w + c->L.cover);
+        sa.cut = w + c->L.cut;
+        if (launch_saturation(sa, c->num_sms, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
+        c->cut_ready = true;
+    }
     // 1. depth sort of all (view, Gaussian) items (digit histograms counted by the preprocess)
     uint32_t* dk[2] = {reinterpret_cast<uint32_t*>(w + c->L.dkey0), reinterpret_cast<uint32_t*>(w + c->L.dkey1)};
     uint32_t* dv[2] = {reinterpret_cast<uint32_t*>(w + c->L.dval0), reinterpret_cast<uint32_t*>(w + c->L.dval1)};
@@ -359,6 +395,16 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     b.num_sms = c->num_sms;
     b.key_hist = reinterpret_cast<uint32_t*>(p + c->P.hist);
     b.key_passes = radix_passes(c->geo.key_bits);
+    if (c->L.truncate && c->geo.n_items > 0) {
+        b.cut = w + c->L.cut;
+        b.G = reinterpret_cast<const uint32_t*>(w + c->L.cover);
+        b.sorted_keys = dk[rb];
+        uint32_t rn;
+        std::memcpy(&rn, &c->s.r_near, sizeof(rn));
+        b.base = rn >> kCutShift;
+        b.total_tiles = (uint32_t)c->geo.total_tiles;
+        b.kcount = reinterpret_cast<uint32_t*>(w + c->L.kcount);
+    }
     if (launch_binning(b, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
     // 3. stable sort of the pairs by tile id
     int rp = 0;

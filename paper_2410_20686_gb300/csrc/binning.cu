@@ -11,7 +11,9 @@
 // of bands 2..5; the columns of further bands are recomputed from its records by band_columns
 // (odgs_common.cuh), exactly as the preprocess counted them. A big item's pairs over its stored
 // bands are one flat range that the warp writes 32 at a time; pole-stretched Gaussians can cover
-// hundreds of tiles.
+// hundreds of tiles. With truncated lists (saturation.cu) an item writes only the pairs of the
+// tiles that keep its depth bucket, compacted in its tile order; the scan uses the kept counts,
+// and items keep the thread or warp emission that their whole footprint would take.
 #include "odgs_common.cuh"
 #include "odgs_internal.h"
 
@@ -33,22 +35,121 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_count_blocks(const uint32_t* __restrict__ sorted_idx,
-                                                              const uint4* __restrict__ rect, uint32_t n_items,
-                                                              unsigned long long* __restrict__ block_sums) {
+// Tiles t of one row run [row + s, row + s + c) (mod tiles_x) with cut[t] >= b, from bucket b's
+// prefix counts G over the tiles.
+__device__ __forceinline__ uint32_t kept_in_run(const uint32_t* G, uint32_t row, int s, int c, int tiles_x) {
+    const int first = min(c, tiles_x - s);
+    uint32_t n = G[row + (uint32_t)(s + first)] - G[row + (uint32_t)s];
+    if (c > first) n += G[row + (uint32_t)(c - first)] - G[row];
+    return n;
+}
+
+// Span (start | count << 16) of stored band b < 6, without a dynamically indexed array.
+__device__ __forceinline__ uint32_t stored_span(uint4 rc, const uint4* rect2, uint32_t idx, int b) {
+    if (b == 0) return rc.z;
+    if (b == 1) return rc.w;
+    const uint4 r2 = rect2[idx];
+    return b == 2 ? r2.x : (b == 3 ? r2.y : (b == 4 ? r2.z : r2.w));
+}
+
+// Pairs per block of 512 depth-sorted items. With truncated lists, the kept pairs of each item
+// (its tiles whose cut keeps its depth bucket), stored per position for the emission: per row
+// band two prefix-count loads, the bands of items with more than six (whose columns are not
+// stored) computed by the warp, one band per lane.
+__global__ void __launch_bounds__(kScanThreads) k_count_blocks(BinArgs a) {
     __shared__ unsigned long long s[kScanThreads / 32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const uint32_t base = blockIdx.x * kScanTile;
     unsigned long long c = 0ull;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
-        uint32_t k = base + i;
-        if (k < n_items) {
-            const uint32_t idx = sorted_idx[k];
+        const uint32_t k = base + i;
+        uint4 rc = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t idx = 0u;
+        if (k < a.n_items) {
+            idx = a.sorted_idx[k];
             // idx >= n_items only after a depth sort that gave up (status already set)
-            if (idx < n_items) c += __ldg(&rect[idx].y);
+            if (idx < a.n_items) rc = a.rect[idx];
         }
+        if (!a.G) {
+            c += rc.y;
+            continue;
+        }
+        const int nb = (int)(rc.x >> 16), ty0 = (int)(rc.x & 0xFFFFu);
+        const int bk = k < a.n_items ? depth_bucket(a.sorted_keys[k], a.base) : 0;
+        const uint32_t* G = a.G + (size_t)bk * (a.total_tiles + 1u);
+        // every tile of the frame keeps this bucket (the items in front of the first cut, among
+        // them the near, large ones with many bands): the whole footprint
+        const bool all = rc.y > 0u && G[a.total_tiles] == a.total_tiles;
+        uint32_t kept = all ? rc.y : 0u;
+        if (rc.y > 0u && !all && nb <= 6) {
+            const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+            const uint4 r2 = nb > 2 ? a.rect2[idx] : make_uint4(0u, 0u, 0u, 0u);
+            for (int b = 0; b < nb; ++b) {
+                const uint32_t sp = b == 0 ? rc.z : (b == 1 ? rc.w : (b == 2 ? r2.x : (b == 3 ? r2.y : (b == 4 ? r2.z : r2.w))));
+                const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
+                if (sp >> 16) kept += kept_in_run(G, row, (int)(sp & 0xFFFFu), (int)(sp >> 16), V.tiles_x);
+            }
+        }
+        // items of more bands (near, large Gaussians, which cluster at the front of the depth
+        // order): queued for k_count_big, which spreads them over all warps
+        const bool many = rc.y > 0u && !all && nb > 6;
+        const unsigned m = __ballot_sync(full, many);
+        if (m) {
+            uint32_t slot = 0u;
+            if (lane == __ffs(m) - 1) slot = atomicAdd(&a.hdr->n_count_big, (uint32_t)__popc(m));
+            slot = __shfl_sync(full, slot, __ffs(m) - 1);
+            if (many) a.big[slot + __popc(m & ((1u << lane) - 1u))] = make_uint2(k, 0u);
+        }
+        if (many) continue;  // k_count_big writes its word and adds its pairs to the block's sum
+        if (k < a.n_items) a.kcount[k] = kept | ((uint32_t)bk << 26);
+        c += kept;
     }
     c = block_sum_u64(c, s);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = c;
+    if (threadIdx.x == 0) a.block_sums[blockIdx.x] = c;
+}
+
+// Kept pairs of the queued items of more than six bands, one warp per item (static round robin),
+// added to their block's sum.
+__global__ void __launch_bounds__(256) k_count_big(BinArgs a) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nq = a.hdr->n_count_big;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nq; i += nwarps) {
+        const uint32_t k = a.big[i].x;
+        const uint32_t idx = a.sorted_idx[k];
+        const uint4 rc = a.rect[idx];
+        const int bk = depth_bucket(a.sorted_keys[k], a.base);
+        const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+        const Footprint fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
+        int jlo, jhi;
+        footprint_rows(fp, V.H, jlo, jhi);
+        const uint32_t* G = a.G + (size_t)bk * (a.total_tiles + 1u);
+        const int nb = (int)(rc.x >> 16), ty0 = (int)(rc.x & 0xFFFFu);
+        uint32_t tot = 0u;
+        for (int gb = 0; gb < nb; gb += 32) {
+            const int b = gb + lane;
+            int start = 0, cnt = 0;
+            if (b < 6) {
+                const uint32_t sp = stored_span(rc, a.rect2, idx, b);
+                start = (int)(sp & 0xFFFFu);
+                cnt = (int)(sp >> 16);
+            } else if (b < nb) {
+                const int ty = ty0 + b, th = a.tile_h;
+                band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, V.model == 0,
+                             start, cnt);
+            }
+            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
+            tot += cnt > 0 ? kept_in_run(G, row, start, cnt, V.tiles_x) : 0u;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(full, tot, o);
+        if (lane == 0) {
+            a.kcount[k] = tot | ((uint32_t)bk << 26);
+            if (tot) atomicAdd(a.block_sums + k / kScanTile, (unsigned long long)tot);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __restrict__ block_sums, int nblocks,
@@ -86,7 +187,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __rest
         hdr->pairs_emitted = used;
         hdr->n_pairs_sort = (uint32_t)used;
         hdr->n_big = 0u;
-        hdr->big_next = 0u;
+        hdr->n_count_big = 0u;
         if (total > capacity) atomicOr(&hdr->status, kStCapacity);
     }
 }
@@ -162,11 +263,31 @@ __device__ __forceinline__ void stored_spans(uint32_t idx, uint4 rc, const EmitA
     }
 }
 
+// Writes the pairs of one row band that keep bucket bk (cut[tile] >= bk), compacted from offset
+// off by one thread, and counts their digits; returns the offset after them.
+__device__ __forceinline__ unsigned long long write_band_kept(uint32_t row, int start, int cnt, int tiles_x,
+                                                              uint32_t idx, int bk, unsigned long long off,
+                                                              const EmitArgs& a, uint32_t (*s_hist)[256]) {
+    for (int k = 0; k < cnt; ++k) {
+        int tx = start + k;
+        if (tx >= tiles_x) tx -= tiles_x;
+        const uint32_t key = row + (uint32_t)tx;
+        if ((int)__ldg(a.cut + key) < bk) continue;
+        if (off < a.capacity) {
+            a.keys[off] = key;
+            a.vals[off] = idx;
+            for (int p = 0; p < a.key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xFFu], 1u);
+        }
+        ++off;
+    }
+    return off;
+}
+
 // Emits all pairs of one item from offset off, by one thread. The spans of the item's first
 // kStoredBands row bands were stored by the preprocess; further bands are recomputed (same
-// functions).
+// functions). bk >= 0: only the pairs of tiles that keep depth bucket bk.
 __device__ __forceinline__ void emit_item_thread(uint32_t idx, uint4 rc, unsigned long long off, const EmitArgs& a,
-                                                 uint32_t (*s_hist)[256]) {
+                                                 uint32_t (*s_hist)[256], int bk) {
     const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
     const int ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
     const int th = a.tile_h;
@@ -177,6 +298,10 @@ __device__ __forceinline__ void emit_item_thread(uint32_t idx, uint4 rc, unsigne
         if (b >= nb) break;
         const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + b) * (uint32_t)V.tiles_x;
         const int cnt = (int)(spans[b] >> 16);
+        if (bk >= 0) {
+            off = write_band_kept(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, bk, off, a, s_hist);
+            continue;
+        }
         write_band(row, (int)(spans[b] & 0xFFFFu), cnt, V.tiles_x, idx, off, a.capacity, 0, 1, a.keys, a.vals,
                    s_hist, a.key_passes);
         off += (unsigned long long)cnt;
@@ -190,8 +315,73 @@ __device__ __forceinline__ void emit_item_thread(uint32_t idx, uint4 rc, unsigne
         band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, V.model == 0, start,
                          cnt);
         const uint32_t row = (uint32_t)V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x;
+        if (bk >= 0) {
+            off = write_band_kept(row, start, cnt, V.tiles_x, idx, bk, off, a, s_hist);
+            continue;
+        }
         write_band(row, start, cnt, V.tiles_x, idx, off, a.capacity, 0, 1, a.keys, a.vals, s_hist, a.key_passes);
         off += (unsigned long long)cnt;
+    }
+}
+
+// The kept pairs of one item (tiles that keep depth bucket bk), by a whole warp: lanes compute the
+// spans of 32 row bands at a time, then the warp takes band after band 32 columns per step and
+// writes the kept ones compacted (ballot order = column order).
+__device__ __forceinline__ void emit_item_warp_kept(uint32_t idx, uint4 rc, unsigned long long off, int bk,
+                                                    const EmitArgs& a, int lane, uint32_t (*s_hist)[256]) {
+    const unsigned full = 0xffffffffu;
+    const ViewDev& V = a.views[idx / (uint32_t)a.n_per_view];
+    const int th = a.tile_h, ty0 = (int)(rc.x & 0xFFFFu), nb = (int)(rc.x >> 16);
+    const uint4 r2 = nb > 2 ? a.rect2[idx] : make_uint4(0u, 0u, 0u, 0u);
+    Footprint fp{};
+    int jlo = 0, jhi = -1;
+    if (nb > kStoredBands) {
+        fp = make_footprint(a.rec_a[idx], a.rec_b[idx]);
+        footprint_rows(fp, V.H, jlo, jhi);
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    for (int gb = 0; gb < nb; gb += 32) {
+        const int b = gb + lane;
+        int start = 0, cnt = 0;
+        if (b < nb) {
+            if (b < kStoredBands) {
+                const uint32_t sp = b == 0 ? rc.z : (b == 1 ? rc.w : (b == 2 ? r2.x : (b == 3 ? r2.y : (b == 4 ? r2.z : r2.w))));
+                start = (int)(sp & 0xFFFFu);
+                cnt = (int)(sp >> 16);
+            } else {
+                const int ty = ty0 + b;
+                band_columns(fp, max(jlo, ty * th), min(jhi, ty * th + th - 1), V.W, a.tile_w, V.tiles_x, V.model == 0,
+                             start, cnt);
+            }
+        }
+        unsigned nz = __ballot_sync(full, cnt > 0);
+        while (nz) {
+            const int l = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const int c = __shfl_sync(full, cnt, l), s0 = __shfl_sync(full, start, l);
+            const uint32_t row = (uint32_t)V.tile_base + (uint32_t)(ty0 + gb + l) * (uint32_t)V.tiles_x;
+            for (int k0 = 0; k0 < c; k0 += 32) {
+                const int k = k0 + lane;
+                uint32_t key = 0u;
+                bool kept = false;
+                if (k < c) {
+                    int tx = s0 + k;
+                    if (tx >= V.tiles_x) tx -= V.tiles_x;
+                    key = row + (uint32_t)tx;
+                    kept = (int)__ldg(a.cut + key) >= bk;
+                }
+                const unsigned km = __ballot_sync(full, kept);
+                if (kept) {
+                    const unsigned long long o = off + (unsigned long long)__popc(km & lt);
+                    if (o < a.capacity) {
+                        a.keys[o] = key;
+                        a.vals[o] = idx;
+                        for (int p = 0; p < a.key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xFFu], 1u);
+                    }
+                }
+                off += (unsigned long long)__popc(km);
+            }
+        }
     }
 }
 
@@ -305,7 +495,10 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
         // an index past the end (only after a depth sort that gave up) emits nothing, as in
         // k_count_blocks, so that the offsets of the two kernels agree
         const uint4 rc = (k < a.n_items && idx < a.n_items) ? a.rect[idx] : make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t cnt = rc.y;
+        // kept pairs (the scan) and the item's whole footprint (thread or warp emission)
+        const uint32_t kw = (a.kcount && k < a.n_items) ? a.kcount[k] : rc.y;
+        const uint32_t cnt = a.kcount ? (kw & 0x3FFFFFFu) : rc.y;
+        const int bk = (a.kcount && cnt < rc.y) ? (int)(kw >> 26) : -1;
         // block-wide exclusive scan of the counts of this round (items in depth order)
         unsigned long long x = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -323,22 +516,23 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(EmitArgs a) {
         __syncthreads();
         if (tid == 0) s_carry += tot;
         // small items: one lane each
-        if (cnt > 0u && cnt <= 32u) emit_item_thread(idx, rc, off, a, s_hist);
+        if (cnt > 0u && rc.y <= 32u) emit_item_thread(idx, rc, off, a, s_hist, bk);
         // large items: queued for k_emit_big (whole warps, dynamically scheduled). Depth order
         // clusters the nearest, largest Gaussians into the first blocks, so serving them here
         // would leave a few warps writing most of the pairs.
-        const unsigned bigm = __ballot_sync(0xffffffffu, cnt > 32u);
+        const bool big = cnt > 0u && rc.y > 32u;
+        const unsigned bigm = __ballot_sync(0xffffffffu, big);
         if (bigm) {  // one queue reservation per warp
             uint32_t base_slot = 0u;
             if (lane == __ffs(bigm) - 1) base_slot = atomicAdd(&a.hdr->n_big, (uint32_t)__popc(bigm));
             base_slot = __shfl_sync(0xffffffffu, base_slot, __ffs(bigm) - 1);
-            if (cnt > 32u) a.big[base_slot + __popc(bigm & ((1u << lane) - 1u))] = make_uint2(idx, (uint32_t)off);
+            if (big) a.big[base_slot + __popc(bigm & ((1u << lane) - 1u))] = make_uint2(k, (uint32_t)off);
         }
     }
     flush_digits(s_hist, a.key_hist, a.key_passes);
 }
 
-__global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
+__global__ void __launch_bounds__(256, 4) k_emit_big(EmitArgs a) {
     __shared__ uint32_t s_hist[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i >> 8][i & 255] = 0u;
     __syncthreads();
@@ -348,7 +542,16 @@ __global__ void __launch_bounds__(256) k_emit_big(EmitArgs a) {
     // static round-robin over the queue: no shared counter to contend on
     for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_big; i += nwarps) {
         const uint2 e = a.big[i];
-        emit_item_warp(e.x, (unsigned long long)e.y, a, lane, s_hist);
+        const uint32_t idx = a.sorted_idx[e.x];
+        if (a.kcount) {
+            const uint4 rc = a.rect[idx];
+            const uint32_t kw = a.kcount[e.x];
+            if ((kw & 0x3FFFFFFu) < rc.y) {
+                emit_item_warp_kept(idx, rc, (unsigned long long)e.y, (int)(kw >> 26), a, lane, s_hist);
+                continue;
+            }
+        }
+        emit_item_warp(idx, (unsigned long long)e.y, a, lane, s_hist);
     }
     flush_digits(s_hist, a.key_hist, a.key_passes);
 }
@@ -393,9 +596,15 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
     cudaError_t e;
     const int nb = scan_blocks_for(a.n_items);
     if (nb > 0) {
-        k_count_blocks<<<nb, kScanThreads, 0, st>>>(a.sorted_idx, a.rect, a.n_items, a.block_sums);
+        if (a.G && (e = cudaMemsetAsync(&a.hdr->n_count_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        k_count_blocks<<<nb, kScanThreads, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
+        if (a.G) {
+            k_count_big<<<a.num_sms * 8, 256, 0, st>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            *launches += 1;
+        }
     }
     k_scan_blocks<<<1, 1024, 0, st>>>(a.block_sums, nb, a.hdr, a.capacity);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -408,6 +617,8 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
         ea.block_offsets = a.block_sums; ea.capacity = a.capacity; ea.keys = a.keys; ea.vals = a.vals;
         ea.big = a.big; ea.hdr = a.hdr;
         ea.key_hist = a.key_hist; ea.key_passes = a.key_passes;
+        ea.kcount = a.G ? a.kcount : nullptr;
+        ea.cut = a.cut;
         if ((e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
         k_emit<<<nb, kScanThreads, 0, st>>>(ea);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

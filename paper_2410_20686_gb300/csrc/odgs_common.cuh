@@ -32,6 +32,8 @@ constexpr float kTMin = 1e-4f;
 // alpha >= 1/255 is decided on the base-2 exponent p of alpha = 2^p: p >= log2(1/255).
 constexpr float kLog2AlphaMin = -7.99435343685886f;
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kLog2_255 = 7.994353436858858f;
 constexpr float kPi = 3.14159265358979323846f;
 
 // device status bits (mirrors ODGS_DEV_* in odgs.h)
@@ -81,7 +83,7 @@ struct Header {
     uint32_t work_fwd;
     uint32_t work_bwd;
     uint32_t n_big;                   // items queued for the warp-wide emission
-    uint32_t big_next;                // work counter of that emission
+    uint32_t n_count_big;             // items queued for the warp-wide kept-pair count
     uint32_t pad[3];
 };
 
@@ -331,6 +333,61 @@ __device__ __forceinline__ void row_terms(float4 con, float du, float dy, float&
 }
 __device__ __forceinline__ float slice_exponent(float4 con, float t, float rowt) {
     return __fmaf_rn(__fmul_rn(con.x, t), t, rowt);
+}
+
+// ------------------------------------------------------------------ saturated-tile truncation
+// A tile's list needs only the entries up to the point where every pixel of the tile has stopped
+// (transmittance below 1e-4): later entries are never evaluated, by the forward or the backward
+// blend. An item that reaches alpha >= a_c >= 1/255 at every pixel centre of a tile multiplies
+// the transmittance of every pixel there by at most 1 - a_c, so once the items of the tile,
+// taken in depth order, have sum -log2(1 - a_c) > log2(1e4) + 0.25 every pixel has stopped
+// (the 0.25 bits cover the rounding of the blend's running products, which have at most 2350
+// factors: each has alpha >= 1/255 and (254/255)^2350 < 1e-4). The sums are kept per depth
+// bucket (kCutShift: four buckets per octave of depth, from r_near), in fixed point with 8
+// fractional bits, rounded down, so that they are exact and independent of the order of the
+// atomic additions: the truncated lists are deterministic.
+constexpr int kCutBuckets = 32;
+constexpr int kCutShift = 21;
+constexpr uint32_t kCutThreshold = 3466;  // ceil((log2(1e4) + 0.25) * 256)
+constexpr uint8_t kCutNone = 255;         // the tile keeps its whole list
+
+// Depth bucket of a depth key (the float bits of a positive depth: monotone in the depth).
+__device__ __forceinline__ int depth_bucket(uint32_t key, uint32_t base) {
+    const int b = (int)(key >> kCutShift) - (int)base;
+    return b < 0 ? 0 : (b >= kCutBuckets ? kCutBuckets - 1 : b);
+}
+
+// 2^p by the hardware's base-2 exponential (relative error below 2^-22; p >= -8 here).
+__device__ __forceinline__ float exp2f_approx(float p) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+    return r;
+}
+
+// Fixed-point weight -log2(1 - a_c) * 256 (rounded down) of an item on the tile of pixel columns
+// [x0, x1] and rows [y0, y1], with a_c a lower bound of the item's alpha at every pixel centre
+// there; 0 if that bound is below 1/255. The exponent's quadratic form is convex, so over the
+// tile its maximum is at one of the four corner pixels; a_c takes a relative 1e-4 off that corner
+// value, far more than the blend's own rounding of the exponent and the error of the hardware's
+// base-2 logarithm and exponential used here (below 2^-21). fc: the column anchor of the image of
+// the item that every column of the tile uses; lo2: log2 of the item's opacity.
+__device__ __forceinline__ uint32_t cover_weight(float4 ra, float4 rb, float lo2, float fc, int r0, int x0, int x1,
+                                                 int y0, int y1) {
+    float qmax = 0.f;
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) {
+        const float dy = __fsub_rn((float)((cy ? y1 : y0) - r0), ra.y);
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+            const float t = __fsub_rn(__fsub_rn(__fsub_rn((float)(cx ? x1 : x0), fc), ra.x), rb.y * dy);
+            qmax = fmaxf(qmax, rb.x * t * t + rb.z * dy * dy);
+        }
+    }
+    const float lp = lo2 - 0.5f * kLog2e * qmax;
+    if (!(lp >= -7.99f)) return 0u;  // alpha < 1/255 (or the opacity is 0)
+    const float ac = fminf(exp2f_approx(lp), kAlphaMax) * (1.f - 1e-4f);
+    if (!(ac >= 1.f / 255.f)) return 0u;
+    return (uint32_t)(-__log2f(1.f - ac) * 256.f);
 }
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {

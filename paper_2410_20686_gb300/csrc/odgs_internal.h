@@ -94,10 +94,18 @@ struct BinArgs {
     Header* hdr;
     unsigned long long capacity;
     uint32_t *keys, *vals;
-    uint2* big;  // [n_items] queue of (item, offset) with more than 32 pairs
+    uint2* big;  // [n_items] queue of (depth-order position, offset) of items with more than 32 pairs
     int num_sms;
     uint32_t* key_hist;  // [passes][256] digit histograms of the emitted tile ids (zeroed here)
     int key_passes;
+    // truncated lists (saturation.cu), or null: per tile the last depth bucket it keeps and per
+    // bucket the prefix counts over the tiles of cut >= bucket; the depth-sorted keys (buckets);
+    // per depth-order position the kept pairs | bucket << 26 (written by k_count_blocks)
+    const uint8_t* cut;
+    const uint32_t* G;
+    const uint32_t* sorted_keys;
+    uint32_t base, total_tiles;
+    uint32_t* kcount;
 };
 
 struct EmitArgs {
@@ -116,7 +124,25 @@ struct EmitArgs {
     Header* hdr;
     uint32_t* key_hist;
     int key_passes;
+    const uint32_t* kcount;  // by depth-order position, or null
+    const uint8_t* cut;
 };
+
+struct SatArgs {
+    const uint4* rect;
+    const float4 *rec_a, *rec_b;
+    const uint32_t* dkey;  // depth keys by item (before the depth sort)
+    const ViewDev* views;
+    int n_per_view;
+    uint32_t n_items, total_tiles;
+    int tile_w, tile_h;
+    uint32_t base;     // depth_bucket's origin: the bits of r_near >> kCutShift
+    uint32_t* cover;   // [kCutBuckets][total_tiles] bucket sums, then [kCutBuckets][total_tiles + 1] prefixes
+    uint8_t* cut;      // [total_tiles]
+};
+// Frames of more tiles keep their whole lists (the bucket tables take 128 bytes per tile).
+constexpr uint32_t kCutMaxTiles = 1u << 19;
+cudaError_t launch_saturation(const SatArgs& a, int num_sms, cudaStream_t st, int* launches);
 
 struct FwdArgs {
     const ViewDev* views;

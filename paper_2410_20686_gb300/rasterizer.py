@@ -31,6 +31,7 @@ class RenderSettings:
     raw_params: bool = False  # scales are log-scales and opacity logits (activated by the kernels)
     pixels_per_thread_bwd: int = 0  # backward blend (0: automatic, 4 where it fits)
     checked: bool = False  # flag (ODGS_DEV_NONFINITE) and cull non-finite parameters / gradients
+    full_lists: bool = False  # keep whole tile lists (default: cut after the tile saturates; same results)
 
     def c_struct(self, sh_coeffs: int) -> L.Settings:
         s = L.Settings()
@@ -44,6 +45,7 @@ class RenderSettings:
         s.raw_params = int(bool(self.raw_params))
         s.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
         s.checked = int(bool(self.checked))
+        s.full_lists = int(bool(self.full_lists))
         return s
 
 

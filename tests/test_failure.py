@@ -21,7 +21,7 @@ def test_pair_capacity_overflow_is_reported_and_the_next_frame_recovers():
     from paper_2410_20686_gb300 import _lib as L
     from paper_2410_20686_gb300.rasterizer import Rasterizer, RenderSettings
     sc = S.random_scene(2000, 256, 128, seed=41, sh_degree=1, radius=(1.0, 5.0))
-    rs = RenderSettings(sh_degree=1)
+    rs = RenderSettings(sh_degree=1, full_lists=True)  # every pair of the footprints is emitted
     params = to_torch(sc)
     probe = Rasterizer()
     probe.forward(*params, sc.views, rs, want_T=False)

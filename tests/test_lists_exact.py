@@ -15,6 +15,8 @@ odgs_debug_lists. For every checked frame:
     bound so that float32 rounding cannot decide it), and no tile lists a Gaussian whose ellipse
     alpha = 1/255 (inflated by the binning's 1e-4 and a further 1e-3) misses the rectangle spanned
     by the tile's pixel centres.
+These checks take the whole lists (full_lists); the lists cut at saturated tiles are prefixes of
+them, checked in tests/test_truncated_lists.py.
 """
 import numpy as np
 import pytest
@@ -29,7 +31,9 @@ NO_KEY = 0xFFFFFFFF
 
 
 def _rs(**kw):
+    # the whole lists: the truncated ones are checked against them (tests/test_truncated_lists.py)
     from paper_2410_20686_gb300.rasterizer import RenderSettings
+    kw.setdefault("full_lists", True)
     return RenderSettings(**kw)
 
 
