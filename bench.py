@@ -157,9 +157,12 @@ def fp32_peak_tflops(torch, dev, peaks):
 #                  opacity 4, colour 12, depth key 4, tile rectangle 12 = 52 B)
 #   bin_sort       per item: four 8-bit depth-sort passes over key + value (16 B each) and the
 #                  digit counts' read of the keys (4 B); the pair count and the emission read the
-#                  sorted index and the rectangle twice (40 B). Per pair: its key + value written
-#                  (8 B), each tile-sort pass (16 B), the range scan's read of the key (4 B).
-#                  Per tile its range (8 B)
+#                  sorted index and the rectangle twice (40 B); the saturation bound's read of
+#                  the rectangle and the conic (32 B); the sorted key read and the kept-pair word
+#                  written and read (12 B). Per sorted pair (the kept prefixes of the tile lists):
+#                  its key + value written (8 B), each tile-sort pass (16 B), the range scan's
+#                  read of the key (4 B). Per tile its range (8 B) and its 32 depth-bucket sums
+#                  and prefix counts zeroed, written and read (3 x 128 B)
 #   preprocess_bwd per Gaussian its parameters read and their gradients written (2 x 236 B); per
 #                  visible item the 9 accumulated screen-space gradients (36 B)
 def param_bytes(sh_degree):
@@ -175,7 +178,7 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
     items, vis, pairs = n, stats["visible"], stats["pairs_sorted"]
     hbm = {
         "preprocess": n * param_bytes(sh_degree) + vis * RECORD_BYTES,
-        "bin_sort": items * (4 * 16 + 4 + 40) + pairs * (8 + 16 * pair_passes + 4) + tiles * 8,
+        "bin_sort": items * (4 * 16 + 4 + 40 + 32 + 12) + pairs * (8 + 16 * pair_passes + 4) + tiles * (8 + 3 * 128),
         "preprocess_bwd": n * 2 * param_bytes(sh_degree) + vis * ACC_BYTES,
     }
     alu = {
@@ -877,7 +880,7 @@ def run_ours(args):
                 "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (max SM clock, "
                              f"{peak_src} peaks file)",
                 "units": {"evals_fwd": stats["evals_fwd"], "evals_bwd": stats["evals_bwd"],
-                          "blended": stats["blended"], "pairs": stats["pairs"],
+                          "blended": stats["blended"], "pairs": stats["pairs"], "pairs_sorted": stats["pairs_sorted"],
                           "entries_tile": stats["entries_tile"], "visible": stats["visible"]}}
     if measured:
         roofline["peak_measured"] = measured

@@ -24,7 +24,9 @@ def test_stage_rooflines_divide_the_stated_work_by_the_stage_time():
     out = bench.stage_rooflines(kern, stats, n=1000, sh_degree=3, tiles=64, pair_passes=1, hbm_gbs=100.0,
                                 alu_tflops=10.0, alu_measured=8.0)
     assert out["preprocess"]["bytes"] == 1000 * 236 + 900 * 52
-    assert out["bin_sort"]["bytes"] == 1000 * (4 * 16 + 4 + 40) + 5000 * (8 + 16 + 4) + 64 * 8
+    # per item: depth passes, digit counts, count + emission reads, the saturation bound's reads, the
+    # sorted key and kept-pair word; per sorted pair; per tile its range and bucket tables
+    assert out["bin_sort"]["bytes"] == 1000 * (4 * 16 + 4 + 40 + 32 + 12) + 5000 * (8 + 16 + 4) + 64 * (8 + 3 * 128)
     assert out["preprocess_bwd"]["bytes"] == 1000 * 2 * 236 + 900 * 36
     assert out["render_fwd"]["flops"] == 11 * 40000 + 12 * 7000
     assert out["render_bwd"]["flops"] == 11 * 30000 + 34 * 7000
