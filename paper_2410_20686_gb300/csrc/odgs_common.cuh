@@ -249,7 +249,11 @@ __device__ __forceinline__ Footprint make_footprint(float4 ra, float4 rb) {
     return f;
 }
 
-__device__ __forceinline__ int floor_div_i(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+// a mod m in [0, m), for any sign of a: a mask when m is a power of two (the common tile counts),
+// else two integer remainders.
+__device__ __forceinline__ int pos_mod(int a, int m) {
+    return (m & (m - 1)) == 0 ? (a & (m - 1)) : ((a % m) + m) % m;
+}
 
 // Pixel rows [jlo, jhi] the footprint can reach (clipped to the image); empty if jlo > jhi.
 __device__ __forceinline__ void footprint_rows(const Footprint& f, int H, int& jlo, int& jhi) {
@@ -302,10 +306,12 @@ __device__ __forceinline__ void band_columns(const Footprint& f, int J0, int J1,
     }
     if (ihi < ilo) return;
     if (ihi - ilo + 1 >= W) { start = 0; count = tiles_x; return; }
-    const int tlo = floor_div_i(ilo, tw), thi = floor_div_i(ihi, tw);
+    // floor division by the tile width, a power of two (8, 16 or 32): an arithmetic shift
+    const int sh = __ffs(tw) - 1;
+    const int tlo = ilo >> sh, thi = ihi >> sh;
     const int n = thi - tlo + 1;
     if (n >= tiles_x) { start = 0; count = tiles_x; return; }
-    start = ((tlo % tiles_x) + tiles_x) % tiles_x;
+    start = pos_mod(tlo, tiles_x);
     count = n;
 }
 

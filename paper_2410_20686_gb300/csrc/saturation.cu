@@ -64,7 +64,7 @@ __device__ __forceinline__ void inner_tiles(float4 ra, float4 rb, float ia, floa
     if (thi < tlo) return;
     if (model == 0) {
         n = min(thi - tlo + 1, tiles_x);
-        start = ((tlo % tiles_x) + tiles_x) % tiles_x;
+        start = pos_mod(tlo, tiles_x);
     } else {
         const int a0 = max(tlo, 0), a1 = min(thi, tiles_x - 1);
         if (a1 >= a0) { start = a0; n = a1 - a0 + 1; }
