@@ -211,8 +211,8 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
 # bench reports null until it is captured again.
 PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh"),
                     "structs": ("odgs_internal.h", "BwdArgs"),
-                    "sha256": "75b2371e9f5110aa2072aafd59988b09542bf9ee94fb3b9a1de6a42539162aea",
-                    "bytes": 171217408}
+                    "sha256": "61f04953bd0f24a87d143c9f151966e0b121e4e711121dff8a157f57cb8205b9",
+                    "bytes": 170833408}
 
 
 def kernel_sources_digest(spec=PROFILED_TRAFFIC):
