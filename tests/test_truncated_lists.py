@@ -96,3 +96,10 @@ def test_cut_lists_other_tile_shape_and_rebuilt_lists():
         assert np.array_equal(cut[2][k], again[k]), k
     for k in NAMES:
         assert rel_l2(g[k], cut[4][k]) < 1e-6, k
+
+
+def test_cut_lists_ragged_rows_and_a_tile_height_of_six():
+    # tiles of 16 x 6 pixels (a tile height that is no power of two) on a 256 x 130 view, whose
+    # last tile row has 4 pixel rows: the coverage bound takes the tile's last pixel row, not a
+    # row past the image
+    _compare(_scene(1200, 8000, 256, 130, seed=13), tile_w=16, tile_h=6)
