@@ -219,7 +219,8 @@ __device__ __forceinline__ void gather_records(const float4* __restrict__ ra, co
 // row band's pixel-centre rows is one interval of columns, so the tiles an item is listed in are
 // exactly the tiles of each row band that meet that interval (seam-wrapped). The preprocess
 // counts them and the emission writes them with these same functions on the same stored floats,
-// in round-to-nearest intrinsics only, so both agree bit for bit.
+// with fixed instructions only (round-to-nearest intrinsics, the hardware's approximate reciprocal
+// and reciprocal square root), so both agree bit for bit.
 struct Footprint {
     int c0, r0;
     float du, dv;
@@ -231,6 +232,13 @@ struct Footprint {
     float ystar;     // dy of the rightmost point, B sqrt(Qb / A)
 };
 
+// The footprint's quotients and square roots in the hardware's approximate reciprocal and
+// reciprocal square root (a few ulp): the footprint only bounds the set alpha >= 1/255, with
+// margins far larger than that (Qb is inflated by 1e-4, the slice edges by 0.01 px), and the same
+// instructions give the same bits wherever it is evaluated.
+__device__ __forceinline__ float fp_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fp_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 __device__ __forceinline__ Footprint make_footprint(float4 ra, float4 rb) {
     Footprint f;
     unpack_anchor(ra.z, f.c0, f.r0);
@@ -239,13 +247,14 @@ __device__ __forceinline__ Footprint make_footprint(float4 ra, float4 rb) {
     f.BC = rb.y;
     f.iC = rb.z;
     f.Qb = rb.w;
-    f.k = __fsqrt_rn(__fdiv_rn(1.f, rb.x));
-    f.ev = __fsqrt_rn(__fdiv_rn(f.Qb, f.iC));
+    const float ia = fp_div(1.f, rb.x);
+    f.k = fp_sqrt(ia);
+    f.ev = fp_sqrt(fp_div(f.Qb, f.iC));
     // Sigma_2D from the slice form without cancellation: C = 1 / gamma, B = beta C, A = 1 / a + beta B
-    const float C = __fdiv_rn(1.f, f.iC);
+    const float C = fp_div(1.f, f.iC);
     const float B = __fmul_rn(f.BC, C);
-    const float A = __fadd_rn(__fdiv_rn(1.f, rb.x), __fmul_rn(f.BC, B));
-    f.ystar = __fmul_rn(B, __fsqrt_rn(__fdiv_rn(f.Qb, A)));
+    const float A = __fadd_rn(ia, __fmul_rn(f.BC, B));
+    f.ystar = __fmul_rn(B, fp_sqrt(fp_div(f.Qb, A)));
     return f;
 }
 
@@ -268,14 +277,14 @@ __device__ __forceinline__ void footprint_rows(const Footprint& f, int H, int& j
 __device__ __forceinline__ int2 footprint_row_range(float4 ra, float4 rb, int H) {
     int c0, r0;
     unpack_anchor(ra.z, c0, r0);
-    const float ev = fminf(__fsqrt_rn(__fdiv_rn(rb.w, rb.z)), 2.f * (float)H);
+    const float ev = fminf(fp_sqrt(fp_div(rb.w, rb.z)), 2.f * (float)H);
     return make_int2(max(0, r0 + (int)ceilf(__fsub_rn(ra.y, ev))), min(H - 1, r0 + (int)floorf(__fadd_rn(ra.y, ev))));
 }
 
 // Horizontal offset of the slice boundary at vertical offset y (side = +1 right, -1 left).
 __device__ __forceinline__ float slice_edge(const Footprint& f, float y, float side) {
     const float q = fmaxf(__fsub_rn(f.Qb, __fmul_rn(__fmul_rn(y, y), f.iC)), 0.f);
-    return __fadd_rn(__fmul_rn(f.BC, y), side * __fmul_rn(f.k, __fsqrt_rn(q)));
+    return __fadd_rn(__fmul_rn(f.BC, y), side * __fmul_rn(f.k, fp_sqrt(q)));
 }
 
 // Tile columns of the band of pixel rows [J0, J1]: start column (mod tiles_x) and count (0 if
