@@ -103,3 +103,29 @@ def test_cut_lists_ragged_rows_and_a_tile_height_of_six():
     # last tile row has 4 pixel rows: the coverage bound takes the tile's last pixel row, not a
     # row past the image
     _compare(_scene(1200, 8000, 256, 130, seed=13), tile_w=16, tile_h=6)
+
+
+def test_cut_lists_on_the_1m_gaussian_frame():
+    # the bench's frame, whose polar tiles saturate after a few hundred of their ~10K entries:
+    # images and T bit for bit, gradients up to the order of the atomic sums, and the cut lists
+    # prefixes of the whole ones on the pole and seam tiles and 64 random tiles
+    sc = S.config2()
+    from paper_2410_20686_gb300.rasterizer import RenderSettings
+    rng = np.random.default_rng(21)
+    weights = [rng.normal(size=(3, v.height, v.width)) for v in sc.views]
+    full = _run(sc, RenderSettings(sh_degree=3, full_lists=True), weights)
+    cut = _run(sc, RenderSettings(sh_degree=3), weights)
+    for a, b in zip(full[0] + full[1], cut[0] + cut[1]):
+        assert np.array_equal(a, b), np.abs(a - b).max()
+    assert cut[3]["pairs_sorted"] < 0.5 * full[3]["pairs_sorted"]
+    fr, cr = full[2]["ranges"].astype(np.int64), cut[2]["ranges"].astype(np.int64)
+    v = sc.views[0]
+    tiles_x = v.width // 16
+    check = [ty * tiles_x + tx for tx, ty in S.stress_tiles(v.width, v.height)]
+    check += list(rng.choice(len(fr), 64, replace=False))
+    for t in check:
+        n = cr[t, 1] - cr[t, 0]
+        assert n <= fr[t, 1] - fr[t, 0]
+        assert np.array_equal(cut[2]["pair_items"][cr[t, 0]:cr[t, 1]], full[2]["pair_items"][fr[t, 0]:fr[t, 0] + n]), t
+    for k in NAMES:
+        assert rel_l2(cut[4][k], full[4][k]) < 1e-6, k
