@@ -337,7 +337,10 @@ odgs_status odgs_get_status(odgs_ctx* c, uint32_t* bits, void* stream) {
     return ODGS_OK;
 }
 
-static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
+// rebuild: the lists of the frame's own earlier binning are rebuilt in the pair buffer (which
+// other frames may have used since); the depth order, the pair counts and their scan are still in
+// the workspace, so only the emission, the tile sort and the ranges run again.
+static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = false) {
     uint8_t* w = c->ws;
     Header* hdr = reinterpret_cast<Header*>(w + c->L.hdr);
     // 0. which tiles saturate, and from which depth on (before the depth sort reorders the keys)
@@ -364,13 +367,15 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
     // 1. depth sort of all (view, Gaussian) items (digit histograms counted by the preprocess)
     uint32_t* dk[2] = {reinterpret_cast<uint32_t*>(w + c->L.dkey0), reinterpret_cast<uint32_t*>(w + c->L.dkey1)};
     uint32_t* dv[2] = {reinterpret_cast<uint32_t*>(w + c->L.dval0), reinterpret_cast<uint32_t*>(w + c->L.dval1)};
-    int rb = 0;
-    if (launch_radix_sort(dk, dv, &hdr->n_items, c->geo.n_items, 32, reinterpret_cast<uint32_t*>(w + c->L.sort_hist),
-                          reinterpret_cast<uint32_t*>(w + c->L.sort_ctr), reinterpret_cast<uint32_t*>(w + c->L.sort_lb),
-                          &hdr->status, c->num_sms, st, &rb, &c->launches, /*hist_ready=*/true,
-                          c->wait_limit) != cudaSuccess)
-        return ODGS_ERR_CUDA;
-    c->depth_buf = rb;
+    int rb = c->depth_buf;
+    if (!rebuild) {
+        if (launch_radix_sort(dk, dv, &hdr->n_items, c->geo.n_items, 32, reinterpret_cast<uint32_t*>(w + c->L.sort_hist),
+                              reinterpret_cast<uint32_t*>(w + c->L.sort_ctr), reinterpret_cast<uint32_t*>(w + c->L.sort_lb),
+                              &hdr->status, c->num_sms, st, &rb, &c->launches, /*hist_ready=*/true,
+                              c->wait_limit) != cudaSuccess)
+            return ODGS_ERR_CUDA;
+        c->depth_buf = rb;
+    }
     // 2. emit (tile, item) pairs in depth order
     uint8_t* p = c->pb;
     uint32_t* pk[2] = {reinterpret_cast<uint32_t*>(p + c->P.keys0), reinterpret_cast<uint32_t*>(p + c->P.keys1)};
@@ -405,6 +410,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st) {
         b.total_tiles = (uint32_t)c->geo.total_tiles;
         b.kcount = reinterpret_cast<uint32_t*>(w + c->L.kcount);
     }
+    b.emit_only = rebuild;
     if (launch_binning(b, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
     // 3. stable sort of the pairs by tile id
     int rp = 0;
@@ -487,9 +493,10 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (c->s.recompute_lists) {
         // the tile lists were not kept (the pair buffer may have served other frames since
-        // odgs_render_fwd): rebuild them from the per-item records, which the workspace still
-        // holds. The binning is deterministic, so the lists are identical to the forward's.
-        odgs_status r = run_bin_sort(c, st);
+        // odgs_render_fwd): rebuild them from the depth order, the pair counts and the per-item
+        // records, which the workspace still holds (emission, tile sort and ranges only). The
+        // binning is deterministic, so the lists are identical to the forward's.
+        odgs_status r = run_bin_sort(c, st, /*rebuild=*/true);
         if (r != ODGS_OK) return r;
     }
     uint8_t* w = c->ws;

@@ -595,7 +595,9 @@ int scan_blocks_for(uint32_t n_items) { return (int)((n_items + kScanTile - 1) /
 cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
     cudaError_t e;
     const int nb = scan_blocks_for(a.n_items);
-    if (nb > 0) {
+    if (a.emit_only) {
+        if ((e = cudaMemsetAsync(&a.hdr->n_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    } else if (nb > 0) {
         if (a.G && (e = cudaMemsetAsync(&a.hdr->n_count_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
         k_count_blocks<<<nb, kScanThreads, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -606,9 +608,11 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
             *launches += 1;
         }
     }
-    k_scan_blocks<<<1, 1024, 0, st>>>(a.block_sums, nb, a.hdr, a.capacity);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *launches += 1;
+    if (!a.emit_only) {
+        k_scan_blocks<<<1, 1024, 0, st>>>(a.block_sums, nb, a.hdr, a.capacity);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 1;
+    }
     if (nb == 0 && (e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
     if (nb > 0) {
         EmitArgs ea{};

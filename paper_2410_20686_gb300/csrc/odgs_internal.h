@@ -106,6 +106,9 @@ struct BinArgs {
     const uint32_t* sorted_keys;
     uint32_t base, total_tiles;
     uint32_t* kcount;
+    // the pair counts, their scan and the kept-pair words of this depth order are in place from an
+    // earlier binning of the same frame: emit only (a rebuild of the lists for the backward pass)
+    bool emit_only;
 };
 
 struct EmitArgs {
