@@ -50,3 +50,20 @@ def test_buckets_are_four_per_octave_of_depth():
     bits = lambda x: struct.unpack("<I", struct.pack("<f", x))[0]
     b = [bits(x) >> shift for x in (1.0, 1.19, 1.25, 1.5, 1.75, 2.0)]
     assert b == sorted(b) and b[0] == b[1] and b[2] == b[0] + 1 and b[5] == b[0] + 4
+
+
+def test_the_exponent_is_largest_at_a_corner_pixel_of_the_tile():
+    # the coverage bound takes alpha at a tile's four corner pixel centres as the smallest over
+    # the tile: the quadratic form a (dx - beta dy)^2 + gamma dy^2 is convex, so over the box of a
+    # tile's pixel centres its maximum is at a corner (brute force over every pixel, float64)
+    import numpy as np
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        a, gam = np.exp(rng.uniform(-8, 2, 2))
+        beta = rng.normal(0, 3)
+        tw, th = int(rng.choice([8, 16, 32])), int(rng.integers(1, 33))
+        x0, y0 = rng.uniform(-200, 200, 2)  # the tile's first pixel centre relative to the mean
+        xs, ys = np.meshgrid(x0 + np.arange(tw), y0 + np.arange(th))
+        q = a * (xs - beta * ys) ** 2 + gam * ys ** 2
+        corners = [q[0, 0], q[0, -1], q[-1, 0], q[-1, -1]]
+        assert q.max() == max(corners)
