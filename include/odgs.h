@@ -14,7 +14,9 @@
  *   -> odgs_render_bwd -> odgs_preprocess_bwd
  * All compute calls are asynchronous on the given CUDA stream (a cudaStream_t passed as void*;
  * NULL = legacy default stream). Only odgs_query_pairs, odgs_get_status and odgs_frame_stats
- * synchronize.
+ * synchronize. odgs_bin_sort also runs work on a stream of the context, forked from the given
+ * stream and joined back to it by events within the call, so the call is ordered on the given
+ * stream as a whole (and can be captured in a CUDA graph from it).
  *
  * Memory: the caller owns every buffer. Device pointers below point to device memory; the
  * structs themselves and the pointer arrays (images, final_T, dL_dimages) live in host memory

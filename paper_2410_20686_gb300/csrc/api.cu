@@ -18,7 +18,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t hdr, views, trig, rec_a, rec_b, rec_c, rect, rect2, dkey0, dkey1, dval0, dval1, block_sums, ranges, T_final,
-        n_last, acc, sort_hist, sort_ctr, sort_lb, big, cover, cut, kcount, total;
+        n_last, acc, sort_hist, sort_ctr, sort_lb, big, cover, cut, kcount, dbucket, total;
     bool truncate;  // the lists are truncated at saturated tiles (the tables below are present)
 };
 
@@ -64,6 +64,7 @@ Layout make_layout(size_t items, const Geometry& g, bool truncate) {
     L.cover = take(sizeof(uint32_t) * (size_t)kCutBuckets * (truncate ? tt + 1 : 0));
     L.cut = take(tt);
     L.kcount = take(truncate ? sizeof(uint32_t) * items : 0);
+    L.dbucket = take(truncate ? items : 0);
     L.total = o;
     return L;
 }
@@ -188,6 +189,15 @@ struct odgs_ctx {
     // workspace (they are computed from the depth keys by item, which the depth sort overwrites,
     // so a second odgs_bin_sort or a rebuild of the lists reuses them)
     bool cut_ready = false;
+    // a second stream on which the binning computes the cuts while the depth sort runs (forked
+    // from and joined back to the caller's stream by events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    ~odgs_ctx() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 
 extern "C" {
@@ -266,6 +276,12 @@ static odgs_status run_preprocess(odgs_ctx* c, cudaStream_t st) {
     a.dkey = reinterpret_cast<uint32_t*>(w + c->L.dkey0);
     a.dval = reinterpret_cast<uint32_t*>(w + c->L.dval0);
     a.dhist = dhist;
+    if (c->L.truncate) {
+        a.dbucket = w + c->L.dbucket;
+        uint32_t rn;
+        std::memcpy(&rn, &c->s.r_near, sizeof(rn));
+        a.cut_base = rn >> kCutShift;
+    }
     a.hdr = hdr;
     if (launch_preprocess(a, c->s.sh_degree, st) != cudaSuccess) return ODGS_ERR_CUDA;
     if (c->n > 0) c->launches += 2;
@@ -343,25 +359,33 @@ odgs_status odgs_get_status(odgs_ctx* c, uint32_t* bits, void* stream) {
 static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = false) {
     uint8_t* w = c->ws;
     Header* hdr = reinterpret_cast<Header*>(w + c->L.hdr);
+    bool joined = true;  // no side-stream work to wait for
     // 0. which tiles saturate, and from which depth on (before the depth sort reorders the keys)
     if (c->L.truncate && !c->cut_ready) {
         SatArgs sa{};
         sa.rect = reinterpret_cast<const uint4*>(w + c->L.rect);
         sa.rec_a = reinterpret_cast<const float4*>(w + c->L.rec_a);
         sa.rec_b = reinterpret_cast<const float4*>(w + c->L.rec_b);
-        sa.dkey = reinterpret_cast<const uint32_t*>(w + c->L.dkey0);
+        sa.dbucket = w + c->L.dbucket;
         sa.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
         sa.n_per_view = c->n > 0 ? c->n : 1;
         sa.n_items = (uint32_t)c->geo.n_items;
         sa.total_tiles = (uint32_t)c->geo.total_tiles;
         sa.tile_w = c->s.tile_w;
         sa.tile_h = c->s.tile_h;
-        uint32_t rn;
-        std::memcpy(&rn, &c->s.r_near, sizeof(rn));
-        sa.base = rn >> kCutShift;
         sa.cover = reinterpret_cast<uint32_t*>(w + c->L.cover);
         sa.cut = w + c->L.cut;
-        if (launch_saturation(sa, c->num_sms, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
+        // on the side stream, beside the depth sort (they share no data; the depth sort's
+        // passes fill only part of the GPU)
+        if (!c->side && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+            return ODGS_ERR_CUDA;
+        if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side, c->ev_fork, 0) != cudaSuccess)
+            return ODGS_ERR_CUDA;
+        if (launch_saturation(sa, c->num_sms, c->side, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
+        if (cudaEventRecord(c->ev_join, c->side) != cudaSuccess) return ODGS_ERR_CUDA;
+        joined = false;
         c->cut_ready = true;
     }
     // 1. depth sort of all (view, Gaussian) items (digit histograms counted by the preprocess)
@@ -411,6 +435,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = fal
         b.kcount = reinterpret_cast<uint32_t*>(w + c->L.kcount);
     }
     b.emit_only = rebuild;
+    if (!joined && cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess) return ODGS_ERR_CUDA;
     if (launch_binning(b, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
     // 3. stable sort of the pairs by tile id
     int rp = 0;

@@ -64,6 +64,8 @@ struct PreArgs {
     uint4* rect2;  // spans of bands 2..5 (items with more than 2 bands)
     uint32_t *dkey, *dval;
     uint32_t* dhist;  // [4][256] digit histograms of dkey (zeroed by k_setup), for the depth sort
+    uint8_t* dbucket;  // per item its depth bucket (saturation.cu), or null
+    uint32_t cut_base;  // depth_bucket's origin
     Header* hdr;
 };
 
@@ -134,12 +136,11 @@ struct EmitArgs {
 struct SatArgs {
     const uint4* rect;
     const float4 *rec_a, *rec_b;
-    const uint32_t* dkey;  // depth keys by item (before the depth sort)
+    const uint8_t* dbucket;  // depth bucket by item (the geometry kernel's)
     const ViewDev* views;
     int n_per_view;
     uint32_t n_items, total_tiles;
     int tile_w, tile_h;
-    uint32_t base;     // depth_bucket's origin: the bits of r_near >> kCutShift
     uint32_t* cover;   // [kCutBuckets][total_tiles] bucket sums, then [kCutBuckets][total_tiles + 1] prefixes
     uint8_t* cut;      // [total_tiles]
 };

@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_geom(PreArgs a) {
                 }
                 a.rect[item] = rect;
                 a.dkey[item] = key;
+                if (a.dbucket) a.dbucket[item] = (uint8_t)depth_bucket(key, a.cut_base);
                 a.dval[item] = (uint32_t)item;
             }
         }

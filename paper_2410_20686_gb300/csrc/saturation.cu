@@ -1,5 +1,5 @@
-// Truncation of the tile lists at saturated tiles (sm_103a). Runs in the binning, before the
-// depth sort, on the preprocess's per-item records:
+// Truncation of the tile lists at saturated tiles (sm_103a). Runs in the binning, on a second
+// stream beside the depth sort, on the preprocess's per-item records and depth buckets:
 //   k_cover   per depth bucket and tile, the fixed-point sum of -log2(1 - a_c) over the items
 //             whose alpha is at least a_c >= 1/255 at every pixel centre of the tile
 //             (cover_weight); an item is examined only if its ellipse is wide enough to hold
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256, 4) k_cover(SatArgs a) {
                     it.f1 = make_float4(rb.x, rb.y, rb.z, __fdividef(1.f, rb.x));
                     nb = (int)(rc.x >> 16);
                     it.i0 = make_int4(c0, r0, (int)(rc.x & 0xFFFFu), nb);
-                    it.i1 = make_int4(depth_bucket(a.dkey[item], a.base), V.W, V.H, V.tiles_x);
+                    it.i1 = make_int4((int)a.dbucket[item], V.W, V.H, V.tiles_x);
                     it.i2 = make_int4(V.tile_base, V.model, 0, 0);
                     s_item[warp][lane] = it;
                 }
