@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 
 #include "odgs_train.h"
 
@@ -286,10 +287,29 @@ __global__ void __launch_bounds__(kThreads) k_ssim_bwd(LossArgs a) {
 __global__ void __launch_bounds__(kThreads) k_l1(LossArgs a) {
     __shared__ float s_red[kThreads / 32];
     float part = 0.f;
+    // 16-byte loads and stores when every row starts on a 16-byte boundary
+    const bool vec = (a.W & 3) == 0 && ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.y) |
+                                         reinterpret_cast<uintptr_t>(a.grad)) & 15u) == 0;
     for (int rc = blockIdx.x; rc < 3 * a.H; rc += gridDim.x) {  // (channel, row) pairs
         const int row = rc % a.H;
         const float w = row_weight(a, row) * a.inv_wsum;
         const size_t base = (size_t)rc * a.W;
+        if (vec) {
+            const float4* x4 = reinterpret_cast<const float4*>(a.x + base);
+            const float4* y4 = reinterpret_cast<const float4*>(a.y + base);
+            for (int c4 = threadIdx.x; c4 < (a.W >> 2); c4 += kThreads) {
+                const float4 xv = x4[c4], yv = y4[c4];
+                const float d[4] = {xv.x - yv.x, xv.y - yv.y, xv.z - yv.z, xv.w - yv.w};
+                float gq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    part = fmaf(w, fabsf(d[k]), part);
+                    gq[k] = d[k] > 0.f ? w : (d[k] < 0.f ? -w : 0.f);
+                }
+                if (a.grad) reinterpret_cast<float4*>(a.grad + base)[c4] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+            }
+            continue;
+        }
         for (int col = threadIdx.x; col < a.W; col += kThreads) {
             const float d = a.x[base + col] - a.y[base + col];
             part = fmaf(w, fabsf(d), part);
