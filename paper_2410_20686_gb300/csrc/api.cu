@@ -30,6 +30,11 @@ struct PairLayout {
 // Truncated lists unless the caller asks for the whole lists or the frame has too many tiles.
 bool truncates(const odgs_settings& s, const Geometry& g) { return !s.full_lists && (uint32_t)g.total_tiles <= kCutMaxTiles; }
 
+// Look-back regions of the two sorts: one per pass, so that one memset clears them (the depth
+// sort's four passes; the tile sort's passes when the tile ids take at most 16 bits).
+constexpr int kDepthLbRegions = 4;
+constexpr int kPairLbRegions = 2;
+
 Layout make_layout(size_t items, const Geometry& g, bool truncate) {
     Layout L{};
     L.truncate = truncate;
@@ -58,7 +63,7 @@ Layout make_layout(size_t items, const Geometry& g, bool truncate) {
     L.acc = take(3 * sizeof(float4) * items);
     L.sort_hist = take(sizeof(uint32_t) * 4 * 256);
     L.sort_ctr = take(sizeof(uint32_t) * 4);
-    L.sort_lb = take(sizeof(uint32_t) * radix_lookback_words(items));
+    L.sort_lb = take(sizeof(uint32_t) * radix_lookback_words(items) * kDepthLbRegions);
     L.big = take(sizeof(uint2) * items);
     const size_t tt = truncate ? (size_t)g.total_tiles : 0;
     L.cover = take(sizeof(uint32_t) * (size_t)kCutBuckets * (truncate ? tt + 1 : 0));
@@ -83,7 +88,7 @@ PairLayout make_pair_layout(size_t cap) {
     P.vals1 = take(sizeof(uint32_t) * cap);
     P.hist = take(sizeof(uint32_t) * 4 * 256);
     P.ctr = take(sizeof(uint32_t) * 4);
-    P.lb = take(sizeof(uint32_t) * radix_lookback_words(cap));
+    P.lb = take(sizeof(uint32_t) * radix_lookback_words(cap) * kPairLbRegions);
     P.total = o;
     return P;
 }
@@ -396,7 +401,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = fal
         if (launch_radix_sort(dk, dv, &hdr->n_items, c->geo.n_items, 32, reinterpret_cast<uint32_t*>(w + c->L.sort_hist),
                               reinterpret_cast<uint32_t*>(w + c->L.sort_ctr), reinterpret_cast<uint32_t*>(w + c->L.sort_lb),
                               &hdr->status, c->num_sms, st, &rb, &c->launches, /*hist_ready=*/true,
-                              c->wait_limit) != cudaSuccess)
+                              c->wait_limit, kDepthLbRegions) != cudaSuccess)
             return ODGS_ERR_CUDA;
         c->depth_buf = rb;
     }
@@ -442,7 +447,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = fal
     if (launch_radix_sort(pk, pv, &hdr->n_pairs_sort, c->pb_cap, c->geo.key_bits, reinterpret_cast<uint32_t*>(p + c->P.hist),
                           reinterpret_cast<uint32_t*>(p + c->P.ctr), reinterpret_cast<uint32_t*>(p + c->P.lb),
                           &hdr->status, c->num_sms, st, &rp, &c->launches, /*hist_ready=*/true,
-                          c->wait_limit) != cudaSuccess)
+                          c->wait_limit, kPairLbRegions) != cudaSuccess)
         return ODGS_ERR_CUDA;
     c->sorted_vals = pv[rp];
     c->pair_buf = rp;
@@ -501,8 +506,10 @@ odgs_status odgs_render_fwd(odgs_ctx* c, float* const* images, float* const* fin
     a.n_last = reinterpret_cast<uint32_t*>(w + c->L.n_last);
     for (int i = 0; i < 3; ++i) a.bg[i] = c->s.bg[i];
     a.hdr = hdr;
-    if (cudaMemsetAsync(&hdr->work_fwd, 0, sizeof(uint32_t), st) != cudaSuccess) return ODGS_ERR_CUDA;
-    if (cudaMemsetAsync(&hdr->evals_fwd, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
+    // the work counter and the forward counters: one memset
+    if (cudaMemsetAsync(&hdr->evals_fwd, 0, reinterpret_cast<uint8_t*>(&hdr->pad1 + 1) - reinterpret_cast<uint8_t*>(&hdr->evals_fwd),
+                        st) != cudaSuccess)
+        return ODGS_ERR_CUDA;
     const int grid = persistent_grid(c, render_fwd_occupancy(c->s.tile_w, c->s.tile_h, a.batch, a.ppt));
     if (launch_render_fwd(a, grid, st) != cudaSuccess) return ODGS_ERR_CUDA;
     c->launches += 1;
@@ -528,8 +535,10 @@ odgs_status odgs_render_bwd(odgs_ctx* c, const float* const* dL, void* stream) {
     Header* hdr = reinterpret_cast<Header*>(w + c->L.hdr);
     float4* acc = reinterpret_cast<float4*>(w + c->L.acc);
     if (cudaMemsetAsync(acc, 0, 3 * sizeof(float4) * c->geo.n_items, st) != cudaSuccess) return ODGS_ERR_CUDA;
-    if (cudaMemsetAsync(&hdr->work_bwd, 0, sizeof(uint32_t), st) != cudaSuccess) return ODGS_ERR_CUDA;
-    if (cudaMemsetAsync(&hdr->evals_bwd, 0, sizeof(unsigned long long), st) != cudaSuccess) return ODGS_ERR_CUDA;
+    // the work counter and the evaluation counter: one memset
+    if (cudaMemsetAsync(&hdr->evals_bwd, 0, reinterpret_cast<uint8_t*>(&hdr->pad0 + 1) - reinterpret_cast<uint8_t*>(&hdr->evals_bwd),
+                        st) != cudaSuccess)
+        return ODGS_ERR_CUDA;
     BwdArgs a{};
     a.views = reinterpret_cast<const ViewDev*>(w + c->L.views);
     a.n_views = c->V; a.total_tiles = c->geo.total_tiles;

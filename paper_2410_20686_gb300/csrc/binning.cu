@@ -153,7 +153,10 @@ __global__ void __launch_bounds__(256) k_count_big(BinArgs a) {
 }
 
 __global__ void __launch_bounds__(1024) k_scan_blocks(unsigned long long* __restrict__ block_sums, int nblocks,
-                                                      Header* hdr, unsigned long long capacity) {
+                                                      Header* hdr, unsigned long long capacity,
+                                                      uint32_t* __restrict__ key_hist) {
+    // the tile sort's digit counts, which the emission adds up, start from 0
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) key_hist[i] = 0u;
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -598,7 +601,7 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
     if (a.emit_only) {
         if ((e = cudaMemsetAsync(&a.hdr->n_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
     } else if (nb > 0) {
-        if (a.G && (e = cudaMemsetAsync(&a.hdr->n_count_big, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        // the kept-count queue counter is 0: cleared by the preprocess's setup and by every scan
         k_count_blocks<<<nb, kScanThreads, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
@@ -609,7 +612,7 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
         }
     }
     if (!a.emit_only) {
-        k_scan_blocks<<<1, 1024, 0, st>>>(a.block_sums, nb, a.hdr, a.capacity);
+        k_scan_blocks<<<1, 1024, 0, st>>>(a.block_sums, nb, a.hdr, a.capacity, a.key_hist);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
     }
@@ -623,7 +626,8 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
         ea.key_hist = a.key_hist; ea.key_passes = a.key_passes;
         ea.kcount = a.G ? a.kcount : nullptr;
         ea.cut = a.cut;
-        if ((e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
+        // zeroed by the scan, except when the scan does not run
+        if (a.emit_only && (e = cudaMemsetAsync(a.key_hist, 0, sizeof(uint32_t) * 4 * 256, st)) != cudaSuccess) return e;
         k_emit<<<nb, kScanThreads, 0, st>>>(ea);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_emit_big<<<a.num_sms * 8, 256, 0, st>>>(ea);

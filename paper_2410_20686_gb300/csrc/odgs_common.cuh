@@ -71,17 +71,20 @@ struct Header {
     unsigned long long pairs;         // total (tile, Gaussian) pairs counted by the preprocess
     unsigned long long pairs_emitted; // min(pairs, capacity) used by the tile sort
     unsigned long long visible;       // (view, Gaussian) items that survived culling
+    // backward-blend counters, contiguous so that one memset clears them
     unsigned long long evals_bwd;     // (pixel, entry) evaluations of the last backward blend
+    uint32_t work_bwd;
+    uint32_t pad0;
     // forward counters, contiguous so that one memset clears them
     unsigned long long evals_fwd;     // (pixel, entry) evaluations of the last forward blend
     unsigned long long blended;       // (pixel, entry) pairs blended by the last forward pass
     unsigned long long entries_tile;  // sum over tiles of the entries processed until all the
                                       // tile's pixels had stopped
+    uint32_t work_fwd;
+    uint32_t pad1;
     uint32_t status;
     uint32_t n_items;                 // views * n
     uint32_t n_pairs_sort;            // 32-bit copy of pairs_emitted for the sort kernels
-    uint32_t work_fwd;
-    uint32_t work_bwd;
     uint32_t n_big;                   // items queued for the warp-wide emission
     uint32_t n_count_big;             // items queued for the warp-wide kept-pair count
     uint32_t pad[3];

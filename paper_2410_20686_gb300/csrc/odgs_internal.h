@@ -190,7 +190,8 @@ size_t radix_lookback_words(size_t max_items);
 constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
-                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit);
+                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit,
+                              int lb_regions = 1);  // look-back regions of radix_lookback_words each
 
 int scan_blocks_for(uint32_t n_items);
 cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches);

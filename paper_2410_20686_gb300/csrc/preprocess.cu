@@ -33,6 +33,8 @@ __global__ void k_setup(ViewTable tab, ViewDev* views, float4* trig, Header* hdr
         hdr->n_pairs_sort = 0u;
         hdr->work_fwd = 0u;
         hdr->work_bwd = 0u;
+        hdr->n_big = 0u;
+        hdr->n_count_big = 0u;  // the binning's queue counters (each binning leaves them at 0)
     }
     for (int e = gid; e < total_trig; e += gridDim.x * blockDim.x) {
         // locate the view and whether e is a column or a row entry

@@ -236,7 +236,8 @@ size_t radix_lookback_words(size_t max_items) {
 // hist_ready the digit histograms of all passes are already in hist (counted by the producer).
 cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_ptr, size_t max_items, int bits,
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
-                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit) {
+                              cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit,
+                              int lb_regions) {
     const int passes = radix_passes(bits);
     *result_buf = 0;
     if (passes == 0 || max_items == 0) return cudaSuccess;
@@ -263,18 +264,24 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
     const size_t lb_words = radix_lookback_words(max_items);
     const int tiles = (int)((max_items + per_cta - 1) / per_cta);
     int cur = 0;
+    // with a look-back region per pass, one memset clears them all; else the one region is
+    // cleared before every pass
+    const bool regions = lb_regions >= passes;
+    if (regions && (e = cudaMemsetAsync(lookback, 0, sizeof(uint32_t) * lb_words * passes, st)) != cudaSuccess)
+        return e;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int pbits = min(8, bits - shift);
-        if ((e = cudaMemsetAsync(lookback, 0, sizeof(uint32_t) * lb_words, st)) != cudaSuccess) return e;
+        uint32_t* lb = regions ? lookback + (size_t)p * lb_words : lookback;
+        if (!regions && (e = cudaMemsetAsync(lb, 0, sizeof(uint32_t) * lb_words, st)) != cudaSuccess) return e;
         if (large)
             k_onesweep<kSortItemsMax><<<max(tiles, 1), kSortThreads, 0, st>>>(
                 k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
-                hist + p * kRadix, lookback, tile_ctrs + p, status, wait_limit);
+                hist + p * kRadix, lb, tile_ctrs + p, status, wait_limit);
         else
             k_onesweep<kSortItemsMax / 2><<<max(tiles, 1), kSortThreads, 0, st>>>(
                 k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
-                hist + p * kRadix, lookback, tile_ctrs + p, status, wait_limit);
+                hist + p * kRadix, lb, tile_ctrs + p, status, wait_limit);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *launches += 1;
         cur ^= 1;
