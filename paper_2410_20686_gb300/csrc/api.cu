@@ -62,8 +62,9 @@ Layout make_layout(size_t items, const Geometry& g, bool truncate) {
     L.n_last = take(sizeof(uint32_t) * (size_t)g.total_pixels);
     L.acc = take(3 * sizeof(float4) * items);
     L.sort_hist = take(sizeof(uint32_t) * 4 * 256);
-    L.sort_ctr = take(sizeof(uint32_t) * 4);
-    L.sort_lb = take(sizeof(uint32_t) * radix_lookback_words(items) * kDepthLbRegions);
+    // the tile counters kCtrBytes before the look-back regions: one memset clears both
+    L.sort_ctr = take(kCtrBytes + sizeof(uint32_t) * radix_lookback_words(items) * kDepthLbRegions);
+    L.sort_lb = L.sort_ctr + kCtrBytes;
     L.big = take(sizeof(uint2) * items);
     const size_t tt = truncate ? (size_t)g.total_tiles : 0;
     L.cover = take(sizeof(uint32_t) * (size_t)kCutBuckets * (truncate ? tt + 1 : 0));
@@ -87,8 +88,8 @@ PairLayout make_pair_layout(size_t cap) {
     P.vals0 = take(sizeof(uint32_t) * cap);
     P.vals1 = take(sizeof(uint32_t) * cap);
     P.hist = take(sizeof(uint32_t) * 4 * 256);
-    P.ctr = take(sizeof(uint32_t) * 4);
-    P.lb = take(sizeof(uint32_t) * radix_lookback_words(cap) * kPairLbRegions);
+    P.ctr = take(kCtrBytes + sizeof(uint32_t) * radix_lookback_words(cap) * kPairLbRegions);
+    P.lb = P.ctr + kCtrBytes;
     P.total = o;
     return P;
 }
@@ -440,6 +441,10 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = fal
         b.kcount = reinterpret_cast<uint32_t*>(w + c->L.kcount);
     }
     b.emit_only = rebuild;
+    if (!rebuild && c->geo.n_items > 0) {  // the pair count clears the ranges
+        b.ranges_zero = reinterpret_cast<uint2*>(w + c->L.ranges);
+        b.n_ranges = (uint32_t)c->geo.total_tiles;
+    }
     if (!joined && cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess) return ODGS_ERR_CUDA;
     if (launch_binning(b, st, &c->launches) != cudaSuccess) return ODGS_ERR_CUDA;
     // 3. stable sort of the pairs by tile id
@@ -453,7 +458,7 @@ static odgs_status run_bin_sort(odgs_ctx* c, cudaStream_t st, bool rebuild = fal
     c->pair_buf = rp;
     // 4. per-tile ranges
     if (launch_tile_ranges(pk[rp], hdr, reinterpret_cast<uint2*>(w + c->L.ranges), c->geo.total_tiles, c->pb_cap,
-                           c->num_sms, st, &c->launches) != cudaSuccess)
+                           c->num_sms, st, &c->launches, /*zeroed=*/b.ranges_zero != nullptr) != cudaSuccess)
         return ODGS_ERR_CUDA;
     return ODGS_OK;
 }

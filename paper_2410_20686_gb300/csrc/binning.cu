@@ -61,6 +61,10 @@ __global__ void __launch_bounds__(kScanThreads) k_count_blocks(BinArgs a) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t base = blockIdx.x * kScanTile;
+    // the tile ranges of this binning start from 0 (k_tile_ranges writes the non-empty ones)
+    if (a.ranges_zero)
+        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n_ranges; t += gridDim.x * blockDim.x)
+            a.ranges_zero[t] = make_uint2(0u, 0u);
     unsigned long long c = 0ull;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
         const uint32_t k = base + i;
@@ -638,9 +642,9 @@ cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches) {
 }
 
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges, int total_tiles,
-                               size_t max_pairs, int num_sms, cudaStream_t st, int* launches) {
-    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st);
-    if (e != cudaSuccess) return e;
+                               size_t max_pairs, int num_sms, cudaStream_t st, int* launches, bool zeroed) {
+    cudaError_t e;
+    if (!zeroed && (e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st)) != cudaSuccess) return e;
     if (max_pairs == 0) return cudaSuccess;
     int blocks = (int)min((max_pairs / 4 + 255) / 256, (size_t)num_sms * 16);
     k_tile_ranges<<<max(blocks, 1), 256, 0, st>>>(keys, hdr, ranges, (uint32_t)total_tiles);

@@ -106,6 +106,8 @@ struct BinArgs {
     const uint8_t* cut;
     const uint32_t* G;
     const uint32_t* sorted_keys;
+    uint2* ranges_zero;  // the tile ranges, cleared by the pair count (or null)
+    uint32_t n_ranges;
     uint32_t base, total_tiles;
     uint32_t* kcount;
     // the pair counts, their scan and the kept-pair words of this depth order are in place from an
@@ -192,11 +194,15 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
                               uint32_t* hist, uint32_t* tile_ctrs, uint32_t* lookback, uint32_t* status, int num_sms,
                               cudaStream_t st, int* result_buf, int* launches, bool hist_ready, uint32_t wait_limit,
                               int lb_regions = 1);  // look-back regions of radix_lookback_words each
+// A sort whose four tile counters lie kCtrBytes before its look-back regions (one per pass) clears
+// both with one memset.
+constexpr size_t kCtrBytes = 256;
 
 int scan_blocks_for(uint32_t n_items);
 cudaError_t launch_binning(const BinArgs& a, cudaStream_t st, int* launches);
+// zeroed: the ranges are already 0 (cleared by the pair count of the same binning)
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Header* hdr, uint2* ranges, int total_tiles,
-                               size_t max_pairs, int num_sms, cudaStream_t st, int* launches);
+                               size_t max_pairs, int num_sms, cudaStream_t st, int* launches, bool zeroed = false);
 
 size_t render_fwd_smem(int batch);
 size_t render_bwd_smem(int batch, int threads);

@@ -242,7 +242,10 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
     *result_buf = 0;
     if (passes == 0 || max_items == 0) return cudaSuccess;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(tile_ctrs, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return e;
+    // tile counters placed kCtrBytes before the look-back regions are cleared with them
+    const bool ctr_with_lb = lb_regions >= passes &&
+                             reinterpret_cast<uint8_t*>(lookback) == reinterpret_cast<uint8_t*>(tile_ctrs) + kCtrBytes;
+    if (!ctr_with_lb && (e = cudaMemsetAsync(tile_ctrs, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return e;
     if (!hist_ready) {
         if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * kRadix, st)) != cudaSuccess) return e;
         int hblocks = (int)min((max_items + 255) / 256, (size_t)num_sms * 8);
@@ -267,7 +270,9 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
     // with a look-back region per pass, one memset clears them all; else the one region is
     // cleared before every pass
     const bool regions = lb_regions >= passes;
-    if (regions && (e = cudaMemsetAsync(lookback, 0, sizeof(uint32_t) * lb_words * passes, st)) != cudaSuccess)
+    if (regions && (e = cudaMemsetAsync(ctr_with_lb ? static_cast<void*>(tile_ctrs) : static_cast<void*>(lookback), 0,
+                                        (ctr_with_lb ? kCtrBytes : 0) + sizeof(uint32_t) * lb_words * passes, st)) !=
+                       cudaSuccess)
         return e;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
