@@ -211,8 +211,8 @@ def stage_rooflines(kern, stats, n, sh_degree, tiles, pair_passes, hbm_gbs, alu_
 # bench reports null until it is captured again.
 PROFILED_TRAFFIC = {"kernel": "k_render_bwd", "sources": ("render_bwd.cu", "odgs_common.cuh"),
                     "structs": ("odgs_internal.h", "BwdArgs"),
-                    "sha256": "6cfaeb14872d380aa4b7e40cd420c28814d56befb702ad017a2b0cb3db9c3379",
-                    "bytes": 170933248}
+                    "sha256": "79548bc8d827a32d6196073bbce0fad16e61150ec889680e230c810e30ee5cfe",
+                    "bytes": 171006208}
 
 
 def kernel_sources_digest(spec=PROFILED_TRAFFIC):
