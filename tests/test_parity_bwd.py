@@ -99,6 +99,30 @@ def test_recomputed_lists_give_the_same_gradients():
         assert rel_l2(b[k], a[k]) < 1e-6, k
 
 
+def test_backward_accumulators_start_from_zero():
+    """The per-(view, Gaussian) accumulators of the backward blend start from zero on every call:
+    a second backward of the same forward, and the next frame after a backward, give the oracle's
+    gradients as the first backward does."""
+    import torch
+    from paper_2410_20686_gb300.rasterizer import Rasterizer
+    sc = S.random_scene(600, 96, 48, seed=99, sh_degree=2, log_scale=(-2.5, 0.5))
+    rs = _rs(sh_degree=2)
+    w = _weights(sc, rs, 5)
+    ref = _oracle_grads(sc, rs, w)
+    rast = Rasterizer()
+    first = _gpu_grads(sc, rs, w, rast)
+    gi = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in w]
+    again = rast.backward(gi)
+    torch.cuda.synchronize()
+    again = {k: v.cpu().numpy().astype(np.float64) for k, v in again.items()}
+    nxt = _gpu_grads(sc, rs, w, rast)
+    for g in (first, again, nxt):
+        _assert_close(g, ref)
+    for k in NAMES:  # the same sums, up to the order of the atomic additions
+        assert rel_l2(again[k], first[k]) < 1e-6, k
+        assert rel_l2(nxt[k], first[k]) < 1e-6, k
+
+
 @pytest.mark.parametrize("tile_w,tile_h,ppt,ppt_bwd", [(16, 16, 2, 4), (32, 8, 1, 1), (32, 16, 2, 2), (8, 8, 1, 2),
                                                      (16, 16, 4, 2)])
 def test_gradients_across_thread_layouts(tile_w, tile_h, ppt, ppt_bwd):
