@@ -99,126 +99,139 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint32_t* __
     __shared__ uint32_t s_keys[kSortThreads * kSortItems];
     __shared__ uint32_t s_vals[kSortThreads * kSortItems];
     __shared__ uint32_t s_scan[kSortWarps];
+    __shared__ uint32_t s_gex[kRadix];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0u;
-    __syncthreads();
-    const uint32_t tile = s_tile;
     const uint32_t n = *n_ptr;
-    const uint32_t base = tile * (uint32_t)(kSortThreads * kSortItems);
-    if (base >= n) return;  // CTA-uniform
     const uint32_t mask = (1u << bits) - 1u;
     const uint32_t lt = (1u << lane) - 1u;
+    // global digit offset of this pass (exclusive scan of the global histogram), the same for
+    // every tile
+    uint32_t tot;
+    s_gex[tid] = block_excl_scan_256(hist[tid], s_scan, tot);
 
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-    const uint32_t wbase = base + (uint32_t)warp * (32u * kSortItems);
+    // Persistent: the grid holds at most the CTAs that fit on the GPU at once (the pair buffer's
+    // capacity, which sizes the sort, is far above the pairs a frame keeps), and each CTA claims
+    // tiles in order until they run out. A tile waits only on tiles claimed before it, by CTAs
+    // that are running, so the look-back always progresses. When the grid has a CTA for every
+    // tile, the CTAs' first claims take them all, and a CTA stops after its first tile.
+    const uint32_t per_cta = (uint32_t)(kSortThreads * kSortItems);
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0u;
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        const uint32_t base = tile * per_cta;
+        if (base >= n) break;  // CTA-uniform: every tile has been claimed
+
+        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+        const uint32_t wbase = base + (uint32_t)warp * (32u * kSortItems);
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
-        const bool valid = idx < n;
-        key[i] = valid ? kin[idx] : 0u;
-        val[i] = valid ? vin[idx] : 0u;
-    }
-    // stable warp-level ranking: items are ordered by (warp, i, lane).
+        for (int i = 0; i < kSortItems; ++i) {
+            const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
+            const bool valid = idx < n;
+            key[i] = valid ? kin[idx] : 0u;
+            val[i] = valid ? vin[idx] : 0u;
+        }
+        // stable warp-level ranking: items are ordered by (warp, i, lane).
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
-        const bool valid = idx < n;
-        const uint32_t d = (key[i] >> shift) & mask;
-        // lanes holding the same digit: a warp match costs more the more distinct digits the warp
-        // holds, so it ranks the last (most significant) pass, where they are few; the others
-        // take one ballot per digit bit (an invalid lane's peers are never used)
-        uint32_t peers;
-        if (use_match) {
-            peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u | (uint32_t)lane));
-        } else {
-            peers = __ballot_sync(0xffffffffu, valid);
+        for (int i = 0; i < kSortItems; ++i) {
+            const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
+            const bool valid = idx < n;
+            const uint32_t d = (key[i] >> shift) & mask;
+            // lanes holding the same digit: a warp match costs more the more distinct digits the
+            // warp holds, so it ranks the last (most significant) pass, where they are few; the
+            // others take one ballot per digit bit (an invalid lane's peers are never used)
+            uint32_t peers;
+            if (use_match) {
+                peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u | (uint32_t)lane));
+            } else {
+                peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                if (b < bits) {
-                    const bool bit = (d >> b) & 1u;
-                    const uint32_t bb = __ballot_sync(0xffffffffu, bit);
-                    peers &= bit ? bb : ~bb;
+                for (int b = 0; b < 8; ++b) {
+                    if (b < bits) {
+                        const bool bit = (d >> b) & 1u;
+                        const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                        peers &= bit ? bb : ~bb;
+                    }
                 }
             }
+            const uint32_t before = valid ? s_warp_hist[warp][d] : 0u;
+            __syncwarp();
+            if (valid && lane == (uint32_t)(__ffs(peers) - 1)) s_warp_hist[warp][d] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            rank[i] = before + (uint32_t)__popc(peers & lt);
         }
-        const uint32_t before = valid ? s_warp_hist[warp][d] : 0u;
-        __syncwarp();
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) s_warp_hist[warp][d] = before + (uint32_t)__popc(peers);
-        __syncwarp();
-        rank[i] = before + (uint32_t)__popc(peers & lt);
-    }
-    __syncthreads();
-    // per digit (one thread each): exclusive prefix over warps, CTA count
-    uint32_t cnt = 0;
-    {
-        const int d = tid;
+        __syncthreads();
+        // per digit (one thread each): exclusive prefix over warps, CTA count
+        uint32_t cnt = 0;
+        {
+            const int d = tid;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            uint32_t c = s_warp_hist[w][d];
-            s_warp_hist[w][d] = cnt;
-            cnt += c;
-        }
-    }
-    // publish this tile's count for digit tid
-    uint32_t* my = lookback + (size_t)tile * kRadix + tid;
-    if (tile == 0) {
-        atomicExch(my, kFlagPrefix | cnt);
-    } else {
-        atomicExch(my, kFlagAgg | cnt);
-    }
-    uint32_t tot;
-    const uint32_t dex = block_excl_scan_256(cnt, s_scan, tot);
-    s_digit_excl[tid] = dex;
-    // global digit offset of this pass (exclusive scan of the global histogram)
-    const uint32_t g = hist[tid];
-    const uint32_t gex = block_excl_scan_256(g, s_scan, tot);
-    // decoupled look-back for digit tid
-    uint32_t excl = 0;
-    if (tile > 0) {
-        int j = (int)tile - 1;
-        uint32_t reads = 0;
-        while (j >= 0) {
-            if (reads++ >= wait_limit) {  // every read counts, so a limit of 0 gives up at once
-                atomicOr(status, kStTimeout);
-                break;
+            for (int w = 0; w < kSortWarps; ++w) {
+                uint32_t c = s_warp_hist[w][d];
+                s_warp_hist[w][d] = cnt;
+                cnt += c;
             }
-            const uint32_t e = ld_volatile(lookback + (size_t)j * kRadix + tid);
-            const uint32_t flag = e & ~kCountMask;
-            if (flag == 0u) {
-                __nanosleep(32);
-                continue;
-            }
-            excl += e & kCountMask;
-            if (flag == kFlagPrefix) break;
-            --j;
         }
-        atomicExch(my, kFlagPrefix | (excl + cnt));
-    }
-    s_base[tid] = gex + excl - dex;
-    __syncthreads();
-    // scatter into shared memory in sorted order within the tile
+        // publish this tile's count for digit tid
+        uint32_t* my = lookback + (size_t)tile * kRadix + tid;
+        if (tile == 0) {
+            atomicExch(my, kFlagPrefix | cnt);
+        } else {
+            atomicExch(my, kFlagAgg | cnt);
+        }
+        const uint32_t dex = block_excl_scan_256(cnt, s_scan, tot);
+        s_digit_excl[tid] = dex;
+        // decoupled look-back for digit tid
+        uint32_t excl = 0;
+        if (tile > 0) {
+            int j = (int)tile - 1;
+            uint32_t reads = 0;
+            while (j >= 0) {
+                if (reads++ >= wait_limit) {  // every read counts, so a limit of 0 gives up at once
+                    atomicOr(status, kStTimeout);
+                    break;
+                }
+                const uint32_t e = ld_volatile(lookback + (size_t)j * kRadix + tid);
+                const uint32_t flag = e & ~kCountMask;
+                if (flag == 0u) {
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += e & kCountMask;
+                if (flag == kFlagPrefix) break;
+                --j;
+            }
+            atomicExch(my, kFlagPrefix | (excl + cnt));
+        }
+        s_base[tid] = s_gex[tid] + excl - dex;
+        __syncthreads();
+        // scatter into shared memory in sorted order within the tile
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
-        if (idx < n) {
-            const uint32_t d = (key[i] >> shift) & mask;
-            const uint32_t pos = s_digit_excl[d] + s_warp_hist[warp][d] + rank[i];
-            s_keys[pos] = key[i];
-            s_vals[pos] = val[i];
+        for (int i = 0; i < kSortItems; ++i) {
+            const uint32_t idx = wbase + (uint32_t)i * 32u + (uint32_t)lane;
+            if (idx < n) {
+                const uint32_t d = (key[i] >> shift) & mask;
+                const uint32_t pos = s_digit_excl[d] + s_warp_hist[warp][d] + rank[i];
+                s_keys[pos] = key[i];
+                s_vals[pos] = val[i];
+            }
         }
-    }
-    __syncthreads();
-    const uint32_t count = min((uint32_t)(kSortThreads * kSortItems), n - base);
-    for (uint32_t p = tid; p < count; p += kSortThreads) {
-        const uint32_t k = s_keys[p];
-        const uint32_t d = (k >> shift) & mask;
-        const uint32_t dst = s_base[d] + p;
-        if (dst < n) {  // only false after a look-back that gave up (status already set)
-            kout[dst] = k;
-            vout[dst] = s_vals[p];
+        __syncthreads();
+        const uint32_t count = min(per_cta, n - base);
+        for (uint32_t p = tid; p < count; p += kSortThreads) {
+            const uint32_t k = s_keys[p];
+            const uint32_t d = (k >> shift) & mask;
+            const uint32_t dst = s_base[d] + p;
+            if (dst < n) {  // only false after a look-back that gave up (status already set)
+                kout[dst] = k;
+                vout[dst] = s_vals[p];
+            }
         }
+        if ((n + per_cta - 1) / per_cta <= gridDim.x) break;
+        // the next tile's first barrier orders these reads of s_keys, s_vals and s_base before
+        // its writes; s_tile and s_warp_hist are not read here
     }
 }
 
@@ -266,6 +279,18 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
     const int per_cta = kSortThreads * (large ? kSortItemsMax : kSortItemsMax / 2);
     const size_t lb_words = radix_lookback_words(max_items);
     const int tiles = (int)((max_items + per_cta - 1) / per_cta);
+    // persistent CTAs: as many as fit at once, at most one per tile
+    static int resident[2] = {0, 0};
+    int& res = resident[large ? 1 : 0];
+    if (res == 0) {
+        int per_sm = 0;
+        if (large)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<kSortItemsMax>, kSortThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<kSortItemsMax / 2>, kSortThreads, 0);
+        res = max(per_sm, 1);
+    }
+    const int grid = max(min(tiles, res * num_sms), 1);
     int cur = 0;
     // with a look-back region per pass, one memset clears them all; else the one region is
     // cleared before every pass
@@ -280,11 +305,11 @@ cudaError_t launch_radix_sort(uint32_t* k[2], uint32_t* v[2], const uint32_t* n_
         uint32_t* lb = regions ? lookback + (size_t)p * lb_words : lookback;
         if (!regions && (e = cudaMemsetAsync(lb, 0, sizeof(uint32_t) * lb_words, st)) != cudaSuccess) return e;
         if (large)
-            k_onesweep<kSortItemsMax><<<max(tiles, 1), kSortThreads, 0, st>>>(
+            k_onesweep<kSortItemsMax><<<grid, kSortThreads, 0, st>>>(
                 k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
                 hist + p * kRadix, lb, tile_ctrs + p, status, wait_limit);
         else
-            k_onesweep<kSortItemsMax / 2><<<max(tiles, 1), kSortThreads, 0, st>>>(
+            k_onesweep<kSortItemsMax / 2><<<grid, kSortThreads, 0, st>>>(
                 k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n_ptr, shift, pbits, p == passes - 1 ? 1 : 0,
                 hist + p * kRadix, lb, tile_ctrs + p, status, wait_limit);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
