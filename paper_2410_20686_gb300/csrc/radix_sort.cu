@@ -9,7 +9,9 @@
 // pass is then one "onesweep" kernel (Adinets & Merrill 2022): a CTA ranks a 2048- or 4096-key
 // tile in shared memory (warp-level ranking by ballots or a match keeps it stable), publishes its per-digit counts,
 // obtains the exclusive prefix of all earlier tiles by decoupled look-back, and writes its keys
-// digit-run by digit-run (coalesced). Look-back waits are bounded: a CTA that has read the
+// digit-run by digit-run (coalesced). The CTAs are persistent (as many as fit on the GPU, each
+// claiming tiles in order), so a sort sized for a capacity far above its keys launches no idle
+// CTAs. Look-back waits are bounded: a CTA that has read the
 // look-back words `wait_limit` times without reaching an inclusive prefix sets kStTimeout in the
 // status word and finishes with a partial prefix; its out-of-range writes are skipped, and every
 // consumer of the sorted arrays bounds the indices it reads.
