@@ -750,11 +750,6 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    # FP32 FMA and exp2f throughput of this device (own microbenchmark), outside the timed region
-    from paper_2410_20686_gb300.rasterizer import measure_peaks
-    measured = measure_peaks(dev) if rank == 0 else None
-    torch.cuda.synchronize()
-
     K = args.steps
     # per-stage times: an eager run of the step with CUDA events between the stages
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
@@ -864,6 +859,12 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
+
+    # FP32 FMA and exp2f throughput of this device (own microbenchmark), after the timed regions:
+    # its seconds of full-rate FMA and MUFU work can leave the SM clock lower for a while
+    from paper_2410_20686_gb300.rasterizer import measure_peaks
+    measured = measure_peaks(dev)
+    torch.cuda.synchronize()
 
     peaks, peak_src = _peaks()
     peak_tf, sms, mhz = fp32_peak_tflops(torch, dev, peaks)
