@@ -285,8 +285,17 @@ def cpu_baseline(scene):
                       f"({r['sample_s']:.1f} s of CPU work); extrapolated"}
 
 
+def workload_config(args, world):
+    """The workload both arms name in their JSON line (the same dict, so that their lines compare)."""
+    return {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2,
+            "sh_degree": 3, "tile": args.tile, "batch": args.batch, "pixels_per_thread": args.ppt,
+            "pixels_per_thread_bwd": args.ppt_bwd,
+            "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
-    _, rank, _ = dist_env()
+    world, rank, _ = dist_env()
     if rank != 0:  # under torchrun only rank 0 times the oracle; the others exit without work
         return
     from paper_2410_20686_gb300 import scenes as S
@@ -308,7 +317,9 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2},
+           "config": workload_config(args, world),
+           "timing": "the FP64 oracle on the host cores, one seeded pixel sample per step, extrapolated to the "
+                     "full frame; value from the median step",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
                             "forward_s_per_frame": statistics.median(fwd),
                             "adjoint_s_per_frame": statistics.median(adj),
@@ -891,13 +902,9 @@ def run_ours(args):
     out = {"metric": METRIC, "value": job_rate(world, K, elapsed), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.width // 2,
-                      "sh_degree": 3, "tile": args.tile, "batch": args.batch, "pixels_per_thread": args.ppt,
-                      "pixels_per_thread_bwd": args.ppt_bwd,
-                      "l2": "inputs larger than L2 (236 MB of parameters read twice per step)",
-                      "timing": "whole fwd+bwd step replayed from a CUDA graph (GraphedFrame), CUDA events around "
-                                "K replays; kernels_ms from an eager run with events between the stages",
-                      "parallelism": f"replicas x{world}"},
+           "config": workload_config(args, world),
+           "timing": "whole fwd+bwd step replayed from a CUDA graph (GraphedFrame), CUDA events around K "
+                     "replays; kernels_ms from an eager run with events between the stages",
            "roofline": roofline, "kernels_ms": kern, "kernels": kernels, "gpu_launches": graph_launches * K,
            "eager_ms_per_step": eager_ms,
            "clocks": clocks, "stage_clocks": stage_clocks}

@@ -58,3 +58,27 @@ def test_clock_summary_reports_median_lowest_and_reasons():
     assert (c["sm_mhz"], c["sm_min_mhz"], c["sm_max_mhz"], c["samples"]) == (2070.0, 2002.0, 2070.0, 3)
     assert c["reasons"] == ["sw_power_cap"] and c["power_w_max"] == 420.5
     assert bench.summarise_clocks([])["sm_mhz"] is None
+
+
+def test_reference_arm_names_the_same_workload_as_the_gpu_arm():
+    """Both arms' JSON lines carry the same config dict (workload_config), so that their lines
+    compare: here the reference arm's line, from a one-step run of the oracle on this host."""
+    import json
+    import subprocess
+    saved = {k: os.environ.pop(k) for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK") if k in os.environ}
+    try:
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                            "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    finally:
+        os.environ.update(saved)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        args = bench.parse()
+    finally:
+        sys.argv = argv
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.workload_config(args, 1)
+    assert line["dtype"] == "f64" and line["higher_is_better"] is True
